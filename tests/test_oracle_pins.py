@@ -1,0 +1,348 @@
+"""Pins of the CPU oracle against facts fixed outside it: published generator outputs, closed
+forms, exact rational arithmetic, finite differences, brute force over permutations, the paper's
+worked example and invariants of the method. CPU only."""
+import itertools
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------- generator
+def test_splitmix64_published_sequence():
+    # First five outputs of SplitMix64 seeded with 0 (Steele, Lea & Flood 2014 generator;
+    # the sequence quoted by reference implementations' test vectors).
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F,
+            0xF88BB8A8724C81EC, 0x1B39896A51A8749B]
+    assert [O.rng(0, i) for i in range(5)] == want
+    assert [int(v) for v in W.rng_u64(0, 0, 5)] == want
+
+
+# ----------------------------------------------------------------------------- key order
+def test_ordbits_is_numeric_order_with_signed_zero():
+    v = np.array([np.inf, -1.0, 2.5, -0.0, 0.0, -np.inf, 1e-30, -1e-30, 3.0e38], dtype=np.float32)
+    u = O.ordbits(v)
+    order = np.argsort(u, kind="stable")
+    expect = [5, 1, 7, 3, 4, 6, 2, 8, 0]  # -inf -1 -1e-30 -0 +0 1e-30 2.5 3e38 inf
+    assert order.tolist() == expect
+    r = W.normal_f32(5000, 11) * np.float32(1e3)
+    np.testing.assert_array_equal(np.argsort(O.ordbits(r), kind="stable"),
+                                  np.argsort(r, kind="stable"))
+    d = np.array([-2.0, -0.0, 0.0, 1.0, np.inf], dtype=np.float64)
+    u = O.ordbits(d).tolist()
+    assert all(a < b for a, b in zip(u, u[1:]))
+
+
+# ----------------------------------------------------------------------------- translate
+def test_translate_maps_sample_range_to_unit_interval():
+    k = W.lognormal_f32(4000, 5, 0.0, 2.0)
+    rows = np.arange(k.shape[0], dtype=np.uint64)
+    for tr in (O.ORDBITS, O.VALUE):
+        nm = O.make_norm(k, rows, tr)
+        x = O.translate_f32(k, nm)
+        assert x.min() == 0.0
+        assert abs(float(x.max()) - 1.0) <= 2 ** -22
+        xd = O.translate_f64(k, nm)
+        assert abs(xd.max() - 1.0) < 1e-12 and xd.min() == 0.0
+        assert np.all(np.diff(x[np.argsort(k)]) >= 0)  # monotone map
+    # VALUE on float32 keys is (key - lo) * scale in binary32
+    nm = O.make_norm(k, rows, O.VALUE)
+    lo = np.float32(k.min())
+    sc = np.float32(1.0 / (float(k.max()) - float(lo)))
+    np.testing.assert_array_equal(O.translate_f32(k, nm), (k - lo) * sc)
+
+
+# ----------------------------------------------------------------------------- model forward
+def test_mlp_forward_closed_form():
+    # y = 2 relu(x) + 3 relu(1 - x) + 0.5
+    p = np.array([1.0, -1.0, 0.0, 1.0, 2.0, 3.0, 0.5], dtype=np.float32)
+    x = np.array([-1.0, 0.0, 0.25, 0.5, 1.0, 2.0], dtype=np.float32)
+    want = [2 * max(v, 0) + 3 * max(1 - v, 0) + 0.5 for v in x.tolist()]
+    np.testing.assert_allclose(O.mlp_forward_f32(1, 2, 0, p, x), want, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(O.mlp_forward_f64(1, 2, 0, p.astype(np.float64), x.astype(np.float64)),
+                               want, rtol=0, atol=1e-15)
+    # two hidden layers: h1 = relu([x, -x]), h2 = relu([h1a - h1b + 1, 2 h1b]), y = h2a + 10 h2b - 1
+    W1 = [1.0, -1.0]; b1 = [0.0, 0.0]
+    W2 = [1.0, -1.0, 0.0, 2.0]; b2 = [1.0, 0.0]
+    W3 = [1.0, 10.0]; b3 = [-1.0]
+    p2 = np.array(W1 + b1 + W2 + b2 + W3 + b3, dtype=np.float32)
+    assert p2.shape[0] == O.num_params(2, 2, 2)
+
+    def ref(v):
+        a, b = max(v, 0), max(-v, 0)
+        return max(a - b + 1, 0) + 10 * max(2 * b, 0) - 1
+    xs = np.array([-3.0, -0.5, 0.0, 0.5, 3.0], dtype=np.float32)
+    np.testing.assert_allclose(O.mlp_forward_f32(2, 2, 2, p2, xs), [ref(v) for v in xs.tolist()],
+                               atol=1e-6)
+
+
+def test_mlp_forward_f32_tracks_f64():
+    for layers, h1, h2 in ((1, 32, 0), (2, 16, 16), (2, 64, 64)):
+        p = O.init_params(layers, h1, h2, 7)
+        x = W.uniform_f32(3000, 3)
+        y32 = O.mlp_forward_f32(layers, h1, h2, p, x).astype(np.float64)
+        y64 = O.mlp_forward_f64(layers, h1, h2, p.astype(np.float64), x.astype(np.float64))
+        scale = np.abs(y64).max() + 1.0
+        assert np.max(np.abs(y32 - y64)) <= 1e-5 * scale
+
+
+# ----------------------------------------------------------------------------- backward
+def _fd_grad(layers, h1, h2, p, x, lab, loss, h=1e-6):
+    g = np.empty_like(p)
+    for i in range(p.shape[0]):
+        pp = p.copy(); pm = p.copy()
+        pp[i] += h; pm[i] -= h
+        lp, _, _ = O.mlp_loss_grad_f64(layers, h1, h2, pp, x, lab, loss)
+        lm, _, _ = O.mlp_loss_grad_f64(layers, h1, h2, pm, x, lab, loss)
+        g[i] = (lp - lm) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("layers,h1,h2,loss", [(1, 8, 0, O.MSE), (2, 5, 4, O.MSE), (2, 6, 3, O.HUBER)])
+def test_mlp_gradient_matches_central_differences(layers, h1, h2, loss):
+    rs = np.random.RandomState(1)
+    p = O.init_params(layers, h1, h2, 3).astype(np.float64)
+    x = rs.uniform(0, 1, 40)
+    lab = rs.uniform(0, 1, 40)
+    L, g, gx = O.mlp_loss_grad_f64(layers, h1, h2, p, x, lab, loss)
+    # keep samples away from ReLU kinks so the loss is smooth within +-h
+    g_fd = _fd_grad(layers, h1, h2, p, x, lab, loss)
+    np.testing.assert_allclose(g, g_fd, rtol=1e-6, atol=1e-8)
+    # input gradient: d mean-loss / d x_i
+    h = 1e-6
+    for i in range(5):
+        xp = x.copy(); xm = x.copy(); xp[i] += h; xm[i] -= h
+        lp, _, _ = O.mlp_loss_grad_f64(layers, h1, h2, p, xp, lab, loss)
+        lm, _, _ = O.mlp_loss_grad_f64(layers, h1, h2, p, xm, lab, loss)
+        assert abs(gx[i] - (lp - lm) / (2 * h)) < 1e-7
+
+
+def test_mlp_gradient_hand_example():
+    # 1 -> 1 -> 1: y = w3 relu(w1 x + b1) + b3 ; MSE over one sample: L = (y - t)^2
+    w1, b1, w3, b3, x, t = 2.0, -0.5, 3.0, 0.25, 0.75, 1.0
+    a = w1 * x + b1           # 1.0
+    y = w3 * a + b3           # 3.25
+    r = y - t                 # 2.25
+    p = np.array([w1, b1, w3, b3])
+    L, g, gx = O.mlp_loss_grad_f64(1, 1, 0, p, np.array([x]), np.array([t]), O.MSE)
+    assert L == pytest.approx(r * r)
+    np.testing.assert_allclose(g, [2 * r * w3 * x, 2 * r * w3, 2 * r * a, 2 * r], rtol=1e-15)
+    assert gx[0] == pytest.approx(2 * r * w3 * w1)
+
+
+def test_huber_loss_closed_form():
+    p = np.array([0.0, 0.0, 0.0, 0.7])  # constant model y = 0.7
+    lab = np.array([0.69, 0.2])          # residuals 0.01 (quadratic) and 0.5 (linear), delta 0.1
+    L, g, _ = O.mlp_loss_grad_f64(1, 1, 0, p, np.zeros(2), lab, O.HUBER, 0.1)
+    want = (0.5 * 0.01 ** 2 + (0.1 * 0.5 - 0.5 * 0.1 ** 2)) / 2
+    assert L == pytest.approx(want, rel=1e-12)
+    assert g[3] == pytest.approx((0.01 + 0.1) / 2, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------- Adam
+def test_adam_first_two_steps_closed_form():
+    lr, b1, b2, eps = 0.1, 0.9, 0.999, 1e-8
+    p = np.array([1.0, -2.0]); m = np.zeros(2); v = np.zeros(2)
+    g1 = np.array([0.5, -4.0])
+    O.adam_f64(p, g1.copy(), m, v, 1, lr, b1, b2, eps)
+    # step 1: m_hat = g, v_hat = g^2  ->  p -= lr * g / (|g| + eps)
+    np.testing.assert_allclose(p, [1.0 - lr * 0.5 / (0.5 + eps), -2.0 + lr * 4.0 / (4.0 + eps)],
+                               rtol=1e-15)
+    p1 = p.copy()
+    g2 = np.array([-1.0, 2.0])
+    O.adam_f64(p, g2.copy(), m, v, 2, lr, b1, b2, eps)
+    mh = ((1 - b1) * b1 * g1 + (1 - b1) * g2) / (1 - b1 ** 2)
+    vh = ((1 - b2) * b2 * g1 ** 2 + (1 - b2) * g2 ** 2) / (1 - b2 ** 2)
+    np.testing.assert_allclose(p, p1 - lr * mh / (np.sqrt(vh) + eps), rtol=1e-14)
+
+
+# ----------------------------------------------------------------------------- slots
+def test_slot_matches_exact_rounding():
+    rs = np.random.RandomState(2)
+    for n in (1, 13, 1000, 1_000_000, 16_777_217, 268_435_456, 3_000_000_000):
+        L, hi, lo = O.nm_split(n, 1.25)
+        assert L == math.floor(n * 1.25) + 1
+        nm = Fraction(n) * Fraction(5, 4)
+        ys = np.concatenate([rs.uniform(0, 1, 300), [0.5, 0.999999, 1e-7]]).astype(np.float32)
+        bad = 0
+        for y in ys.tolist():
+            exact = Fraction(y) * nm + Fraction(1, 2)
+            want = min(math.floor(exact), L - 1)
+            got = O.slot1(y, hi, lo, L)
+            frac = exact - math.floor(exact)
+            if got != want:
+                # only allowed when the exact value sits within 2^-16 of an integer boundary
+                assert abs(got - want) == 1 and (frac < Fraction(1, 65536) or frac > 1 - Fraction(1, 65536))
+                bad += 1
+        assert bad <= 2
+    L, hi, lo = O.nm_split(100, 1.25)
+    assert O.slot1(0.0, hi, lo, L) == 0
+    assert O.slot1(-3.0, hi, lo, L) == 0
+    assert O.slot1(float("nan"), hi, lo, L) == 0
+    assert O.slot1(1.0, hi, lo, L) == L - 1
+    assert O.slot1(7.0, hi, lo, L) == L - 1
+    assert O.slot1(0.5, hi, lo, L) == 63          # 0.5 * 125 + 0.5 = 63.0
+    assert O.slot1(0.1, 10.0, 0.0, 11) == 1       # round(1.0000000149) = 1
+    assert O.slot1(0.25, 10.0, 0.0, 11) == 3      # 2.5 rounds half up
+
+
+# ----------------------------------------------------------------------------- NN-sort
+def _stable_expect(keys, payload=None):
+    order = np.argsort(O.ordbits(keys), kind="stable")
+    return keys[order], (None if payload is None else payload[order])
+
+
+def test_worked_example_of_the_paper():
+    ex = json.load(open(os.path.join(GOLDEN, "example1.json")))
+    keys = np.array(ex["keys"], dtype=np.float32)
+    L, _, _ = O.nm_split(len(keys), ex["m"])
+    out, _, st, fate = O.nnsort(keys, np.array(ex["slots"]), L, ex["eps"], ex["tau"], want_fate=True)
+    e = ex["expect"]
+    assert st["t"] == e["rounds"]
+    assert st["w_size"][1] == e["conflicts_round1"]
+    assert st["placed"][1] == e["placed_round2"]
+    assert st["w_size"][2] == e["conflicts_round2"]
+    assert out.tolist() == e["sorted"]
+    for k in e["in_round1_conflicts"]:
+        assert fate[ex["keys"].index(k)] != 1
+    for k in e["placed_round1"]:
+        assert fate[ex["keys"].index(k)] == 1
+    # worked by hand from the algorithm for this slot map: o_1 stores 7 elements, all in order;
+    # o_2 = (31, 3, 59, 92) in position order, so 3 is the one out-of-order insert.
+    assert st["placed"] == [7, 4] and st["out_of_order"] == [0, 1]
+    assert fate[ex["keys"].index(3)] == -2 and fate[ex["keys"].index(37)] == 0
+
+
+def test_hand_examples_first_arrival_and_out_of_order():
+    keys = np.array([5, 3, 8, 1, 9, 2], dtype=np.float32)
+    L = 8
+    # round 1 stores rows 3,1,0,4 (slots 0,2,3,6); rows 2 and 5 collide; round 2 stores both
+    out, _, st, fate = O.nnsort(keys, np.array([3, 2, 3, 0, 6, 2]), L, eps=2, tau=0, want_fate=True)
+    assert st == {"t": 2, "eps": 2, "n": 6, "L": 8, "tau": 0, "w_size": [6, 2, 0],
+                  "placed": [4, 2], "out_of_order": [0, 0]}
+    assert fate.tolist() == [1, 1, 2, 1, 1, 2]
+    assert out.tolist() == [1, 2, 3, 5, 8, 9]
+    # all positions distinct but not monotone: o_1 = (1, 8, 3, 5, 2, 9) -> 3, 5, 2 are inserted
+    out, _, st, fate = O.nnsort(keys, np.array([3, 2, 1, 0, 6, 4]), L, eps=3, tau=0, want_fate=True)
+    assert st["t"] == 1 and st["w_size"] == [6, 0] and st["out_of_order"] == [3]
+    assert fate.tolist() == [-1, -1, 1, 1, 1, -1]
+    assert out.tolist() == [1, 2, 3, 5, 8, 9]
+    # first arrival wins a shared position: row 0 is stored, row 1 goes to the conflict array
+    out, _, st, fate = O.nnsort(np.array([7, 4], dtype=np.float32), np.array([1, 1]), 3, eps=1, tau=0,
+                                want_fate=True)
+    assert fate.tolist() == [1, 0] and st["w_size"] == [2, 1] and out.tolist() == [4, 7]
+
+
+def test_special_cases():
+    rs = np.random.RandomState(3)
+    keys = rs.permutation(500).astype(np.float32)
+    n = keys.shape[0]
+    L, _, _ = O.nm_split(n)
+    # monotone, distinct positions: one round, nothing conflicts, nothing out of order
+    slots = (keys.astype(np.int64) * 5 // 4).astype(np.uint32)
+    out, _, st, _ = O.nnsort(keys, slots, L, eps=3, tau=0)
+    assert st["t"] == 1 and st["w_size"] == [n, 0] and st["out_of_order"] == [0]
+    # one shared position: each round stores exactly one element
+    out, _, st, _ = O.nnsort(keys, np.full(n, 7, np.uint32), L, eps=4, tau=0)
+    assert st["w_size"] == [n, n - 1, n - 2, n - 3, n - 4] and st["placed"] == [1, 1, 1, 1]
+    np.testing.assert_array_equal(out, np.sort(keys))
+    # count(w) <= tau from the start: no rounds, plain sort
+    out, _, st, _ = O.nnsort(keys, slots, L, eps=3, tau=n)
+    assert st["t"] == 0 and st["w_size"] == [n]
+    np.testing.assert_array_equal(out, np.sort(keys))
+    # eps = 0
+    out, _, st, _ = O.nnsort(keys, slots, L, eps=0, tau=0)
+    assert st["t"] == 0
+    # empty and single inputs
+    out, _, st, _ = O.nnsort(np.zeros(0, np.float32), np.zeros(0, np.uint32), 1, 3, 0)
+    assert out.shape[0] == 0 and st["t"] == 0
+    out, _, st, _ = O.nnsort(np.array([4.0], np.float32), np.array([0], np.uint32), 2, 3, 0)
+    assert out.tolist() == [4.0] and st["t"] == 1
+
+
+def test_brute_force_all_permutations_small():
+    base = np.array([2.0, -0.0, 0.0, 2.0, -1.5, 7.0], dtype=np.float32)
+    rs = np.random.RandomState(4)
+    for n in (1, 2, 3, 4, 5, 6):
+        L, _, _ = O.nm_split(n)
+        for perm in itertools.permutations(range(n)):
+            keys = base[list(perm)]
+            payload = np.arange(n, dtype=np.int32)
+            for mode in range(3):
+                if mode == 0:
+                    slots = np.full(n, L - 1, np.uint32)
+                elif mode == 1:
+                    slots = np.arange(n, dtype=np.uint32)[::-1].copy()
+                else:
+                    slots = rs.randint(0, L, n).astype(np.uint32)
+                for eps, tau in ((1, 0), (3, 0), (2, 1)):
+                    out, outp, st, _ = O.nnsort(keys, slots, L, eps, tau, payload)
+                    # brute force: the unique (key, row)-ordered arrangement
+                    ordk = O.ordbits(keys)
+                    want = sorted(range(n), key=lambda r: (int(ordk[r]), r))
+                    assert outp.tolist() == want
+                    assert out.view(np.uint32).tolist() == keys[want].view(np.uint32).tolist()
+                    assert sum(st["placed"]) + st["w_size"][st["t"]] == n
+
+
+def test_large_random_against_library_stable_sort():
+    keys = W.lognormal_dup_f32(200_000, 9, 0.0, 2.0)
+    payload = np.arange(keys.shape[0], dtype=np.int32)
+    model, _, hist = O.train(keys, layers=1, h1=32, sample_n=2000, steps=100, lr=1e-2, seed=1)
+    assert hist[-1] < hist[0]
+    out, outp, st, fate = O.nnsort_model(keys, model, payload=payload, want_fate=True)
+    ek, ep = _stable_expect(keys, payload)
+    np.testing.assert_array_equal(out.view(np.uint32), ek.view(np.uint32))
+    np.testing.assert_array_equal(outp, ep)
+    # stats and fate agree with each other
+    for i in range(st["t"]):
+        assert np.count_nonzero(np.abs(fate) == i + 1) == st["placed"][i]
+        assert np.count_nonzero(fate == -(i + 1)) == st["out_of_order"][i]
+        assert st["w_size"][i] - st["placed"][i] == st["w_size"][i + 1]
+    assert np.count_nonzero(fate == 0) == st["w_size"][st["t"]]
+    # random positions, uint64 and float64 keys
+    rs = np.random.RandomState(5)
+    for keys in (rs.randint(0, 2 ** 62, 50_000, dtype=np.int64).astype(np.uint64) * np.uint64(3),
+                 rs.standard_normal(50_000)):
+        L, _, _ = O.nm_split(keys.shape[0])
+        out, _, _, _ = O.nnsort(keys, rs.randint(0, L, keys.shape[0]).astype(np.uint32), L, 3, 100)
+        np.testing.assert_array_equal(out, np.sort(keys, kind="stable"))
+
+
+def test_sample_labels_and_training():
+    keys = W.uniform_f32(50_000, 0)
+    rows, nm, x, lab = O.sample_labels(keys, 500, 0, O.VALUE)
+    # the sample is sorted, labels are j/S, inputs of the extremes are 0 and ~1
+    u = O.ordbits(keys[rows.astype(np.int64)]).tolist()
+    assert all(a <= b for a, b in zip(u, u[1:]))
+    np.testing.assert_array_equal(lab, (np.arange(500) / 500).astype(np.float32))
+    assert x[0] == 0.0 and abs(x[-1] - 1.0) < 1e-6
+    # the sample indices are the generator's draws mapped to [0, n)
+    draws = W.rng_u64(O.lib().orc_stream_seed(0, 1), 0, 500)
+    idx = sorted(((int(d) * 50_000) >> 64) for d in draws)
+    assert sorted(rows.tolist()) == idx
+    # uniform keys have a linear CDF: a trained model fits it closely
+    model, _, hist = O.train(keys, 1, 32, 0, O.VALUE, sample_n=500, steps=300, lr=1e-2, seed=0)
+    assert hist[-1] < 1e-3 < hist[0]
+    y = O.mlp_forward_f64(1, 32, 0, model.params.astype(np.float64), np.linspace(0.05, 0.95, 19))
+    np.testing.assert_allclose(y, np.linspace(0.05, 0.95, 19), atol=0.05)
+    # minibatch training follows the batch stream deterministically
+    m1, p1, h1 = O.train(keys, 1, 8, 0, O.VALUE, sample_n=500, steps=20, batch=64, seed=3)
+    m2, p2, h2 = O.train(keys, 1, 8, 0, O.VALUE, sample_n=500, steps=20, batch=64, seed=3)
+    np.testing.assert_array_equal(p1, p2)
+
+
+def test_nan_keys_rejected():
+    keys = np.array([1.0, np.nan, 2.0], dtype=np.float32)
+    model = O.Model(1, 2, 0, O.make_norm(keys[[0, 2]], np.arange(2, dtype=np.uint64), O.VALUE),
+                    O.init_params(1, 2, 0, 0))
+    with pytest.raises(ValueError):
+        O.predict_slots(keys, model)
