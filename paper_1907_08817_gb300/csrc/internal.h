@@ -1,0 +1,165 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "nnsort.h"
+
+namespace nns {
+
+// counts kernels launched by the library (nnsort_launch_count)
+void note_launch(int kernels);
+
+struct Seg;
+struct SegStats;
+struct OKey;
+
+constexpr int RADIX_MAX_BITS = 9;
+constexpr int RADIX_BINS = 1 << RADIX_MAX_BITS;  // 512
+constexpr int PART_THREADS = 512;
+constexpr int PART_ITEMS = 8;
+constexpr int PART_TILE = PART_THREADS * PART_ITEMS;  // 4096
+constexpr int PRED_THREADS = 256;
+constexpr int PRED_ITEMS = 8;
+constexpr int PRED_TILE = PRED_THREADS * PRED_ITEMS;  // 2048
+constexpr int MAX_PASSES = 4;
+
+struct PassPlan {
+    int npass;
+    int wlog;                 // log2 of the bucket width in positions
+    int shift[MAX_PASSES];    // digit shift applied to the global position
+    int bits[MAX_PASSES];
+};
+
+// padded architecture actually instantiated on the device
+struct PadArch {
+    int layers, h1, h2;  // padded widths (8, 16, 32 or 64; h2 = 0 for one hidden layer)
+};
+PadArch pad_arch(int layers, int h1, int h2);
+size_t padded_param_count(const PadArch &a);
+
+// ---- predict (k_predict.cu)
+// Fills gs (global position per element), optional key / payload / row copies into the element
+// space and the per-pass digit histograms hist[npass][RADIX_BINS]. Also serves nnsort_predict
+// through slots_out / y_out (element space of a single array).
+struct PredictArgs {
+    const Seg *segs;
+    int nseg;
+    uint32_t total_tiles;
+    PassPlan plan;
+    uint32_t *gs;            // nullable
+    void *key_copy;          // nullable
+    uint32_t *pay_copy;      // nullable
+    uint32_t *row_init;      // nullable
+    uint32_t *hist;          // nullable
+    uint32_t *slots_out;     // nullable
+    float *y_out;            // nullable
+    uint32_t *err;
+    int key_bytes;
+    int dtype;
+};
+cudaError_t launch_predict(const PadArch &a, int precision, const PredictArgs &p, int sms,
+                           cudaStream_t s);
+
+// ---- partition (k_partition.cu)
+struct OnesweepArgs {
+    uint64_t N;
+    const uint32_t *gs_in;  uint32_t *gs_out;   // null when sorting by key bits
+    const void *key_in;     void *key_out;
+    const uint32_t *pay_in; uint32_t *pay_out;  // nullable
+    const uint32_t *row_in; uint32_t *row_out;  // nullable
+    int key_digits;         // 1: digit from the key's order image, 0: from gs
+    int shift, bits;
+    const uint32_t *digit_base;       // [RADIX_BINS] exclusive global offsets of this pass
+    unsigned long long *lookback;     // [tiles * RADIX_BINS]
+    uint32_t *ticket;
+    uint32_t epoch;
+    uint32_t *err;
+    int key_bytes, dtype;
+};
+cudaError_t launch_onesweep(const OnesweepArgs &a, cudaStream_t s);
+// exclusive scans of the per-pass histograms -> digit bases
+cudaError_t launch_digit_bases(const uint32_t *hist, uint32_t *bases, int npass, cudaStream_t s);
+// histogram of key digits for a key sort
+cudaError_t launch_key_hist(const void *keys, uint64_t N, int key_bytes, int dtype, int npass,
+                            uint32_t *hist, cudaStream_t s);
+// bucket starts by binary search over the partitioned global positions
+cudaError_t launch_bucket_bounds(const uint32_t *gs, uint64_t N, uint32_t nb, int wlog,
+                                 uint32_t *bstart, cudaStream_t s);
+
+// ---- rounds / finalize / polish / seam / repair (k_solve.cu)
+struct SolveArgs {
+    const Seg *segs;
+    int nseg;
+    uint32_t NB;
+    int wlog;
+    const uint32_t *bstart;   // [NB + 1]
+    const uint32_t *gs;       // partitioned
+    const void *keys;         // partitioned
+    const uint32_t *pay;      // partitioned, nullable
+    const uint32_t *rows;     // partitioned, nullable
+    uint8_t *rank;            // [N]
+    SegStats *stats;          // [nseg]
+    OKey *bmax;               // [NB * MAXR]
+    OKey *carry;              // [NB * MAXR]
+    OKey *blo, *bhi;          // [NB]
+    // global scratch for buckets beyond on-chip capacity
+    uint8_t *g_flag;          // [N]
+    uint32_t *g_x, *g_y, *g_r;  // [N] each
+    int8_t *fate;             // nullable, per row (single array only)
+    uint32_t *out_rows;       // [N] rows of the output order (when rows are carried)
+    void *key_scratch;        // [N] free partition buffer reused by the seam repair
+    uint32_t *pay_scratch, *row_scratch;
+    uint32_t *err;
+    int key_bytes, dtype;
+    int polish_cap;           // elements a bucket may hold on chip
+    size_t polish_smem;
+};
+cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s);
+cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s);
+cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s);
+cudaError_t launch_seam_repair(const SolveArgs &a, cudaStream_t s);
+int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks_per_sm,
+                    size_t *smem_bytes);
+
+// ---- training (k_train.cu)
+cudaError_t launch_sample(const void *keys, uint64_t n, int key_bytes, int dtype, uint64_t S,
+                          uint64_t stream_seed, void *sample_keys, uint32_t *sample_rows,
+                          uint32_t *err, cudaStream_t s);
+cudaError_t launch_minmax_norm(const void *sorted_keys, uint64_t S, int key_bytes, int dtype,
+                               int translate, double *norm_out /*lo_val, scale*/,
+                               unsigned long long *lobits_out, cudaStream_t s);
+cudaError_t launch_make_xy(const void *sorted_keys, uint64_t S, int key_bytes, const Norm *nm_dev,
+                           float *x, float *label, cudaStream_t s);
+struct TrainStepArgs {
+    float *params;        // padded layout, updated in place
+    float *m, *v;         // Adam moments (padded layout)
+    float *grad;          // padded layout
+    float *partials;      // [blocks * P]
+    float *loss_partials; // [blocks]
+    float *loss_out;      // [steps]
+    const float *x, *label;
+    uint64_t S;
+    uint32_t batch;       // 0 = full
+    uint64_t batch_seed;
+    int step;             // 0-based
+    int loss; float delta;
+    float lr, b1, b2, eps;
+    size_t P;
+    const float *mask;    // 1 for real parameters, 0 for padding
+};
+cudaError_t launch_train_step(const PadArch &a, const TrainStepArgs &t, cudaStream_t s);
+int train_grad_blocks(uint64_t nsamples);
+// forward / backward / loss-grad for explicit arrays (nnsort_mlp_* entry points)
+cudaError_t launch_mlp_forward(const PadArch &a, const float *params, const float *x, uint64_t n,
+                               float *y, cudaStream_t s);
+cudaError_t launch_mlp_backward(const PadArch &a, const float *params, const float *x,
+                                const float *gy, const float *label, uint64_t n, int mode,
+                                int loss, float delta, float *partials, float *loss_partials,
+                                float *gx, cudaStream_t s, int *blocks_out);
+cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, float *out,
+                                   const float *loss_partials, float *loss_out, float scale,
+                                   cudaStream_t s);
+
+}  // namespace nns

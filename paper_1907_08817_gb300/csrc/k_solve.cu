@@ -1,0 +1,712 @@
+// k_solve.cu -- the Sorting and Polish phases of NN-sort on buckets of positions.
+//
+// After the partition, the elements whose positions fall into bucket b (positions
+// [b W, (b+1) W) of one array) are contiguous and in input order. Because every element keeps
+// its position in every iteration (same f, same scale), the paper's iterations decompose over
+// buckets exactly:
+//   k_rounds   -- Fig. "Algorithm NN-sort" lines 3-14 inside one bucket: each iteration clears
+//                 o_i, lets every still-unplaced element claim its position (the first to arrive,
+//                 i.e. the lowest input row, wins -- "only the first element is stored"), and sends
+//                 the others on to the next conflict array. Output: the iteration in which each
+//                 element was stored (or eps if never), |w_i| contributions, and per-iteration
+//                 maxima of the stored elements for the polish's carry across buckets.
+//   k_finalize -- the loop condition "i < eps and count(w) > tau" over the array's totals
+//                 gives t; exclusive prefix maxima of the per-bucket maxima give the carries.
+//   k_polish   -- Fig. "Algorithm polish" inside one bucket: o_i's stored elements in position
+//                 order; an element smaller than the largest earlier element of o_i (carry from
+//                 earlier buckets included) is out of order and joins the leftover, the rest form
+//                 a sorted run R_i; the last conflict array plus the out-of-order elements are
+//                 sorted (radix sort by key, stable); A' <- merge(A', R_i) for i = 1..t.
+//   k_seam     -- the buckets' outputs are each sorted; where a non-monotone f lets a later
+//                 bucket hold a key smaller than an earlier bucket's, the affected range is
+//                 located and re-sorted (the polish Remark: out-of-order elements end up at their
+//                 correct positions whatever the model's errors).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nns {
+static inline cudaError_t nns_launched(cudaError_t e, int k = 1) {
+    if (e == cudaSuccess) note_launch(k);
+    return e;
+}
+}  // namespace nns
+
+namespace nns {
+
+constexpr int SOLVE_THREADS = 512;
+constexpr int SNW = SOLVE_THREADS / 32;
+constexpr int ROUND_ITEMS = 16;
+constexpr int ROUND_CAP = SOLVE_THREADS * ROUND_ITEMS;  // 8192
+
+__device__ __forceinline__ int seg_of_bucket(const Seg *segs, int nseg, uint32_t b) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].bbase <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename W> __device__ __forceinline__ W ldk(const void *p, size_t i) {
+    return reinterpret_cast<const W *>(p)[i];
+}
+
+__device__ __forceinline__ KMax kmax_none() { KMax r; r.k = 0; r.tb = 0; r.valid = 0; return r; }
+
+// block reduction of an array of MAXR maxima (one per iteration); result in out[] on all threads
+__device__ void block_reduce_kmax_rounds(KMax *v, int eps, KMax *sm /*[SNW][MAXR]*/, KMax *out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int r = 0; r < eps; ++r) {
+        KMax x = v[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            KMax y;
+            y.k = __shfl_down_sync(0xFFFFFFFFu, x.k, o);
+            y.tb = __shfl_down_sync(0xFFFFFFFFu, x.tb, o);
+            y.valid = __shfl_down_sync(0xFFFFFFFFu, x.valid, o);
+            x = kmax(x, y);
+        }
+        if (lane == 0) sm[w * MAXR + r] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)eps) {
+        KMax x = kmax_none();
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) x = kmax(x, sm[ww * MAXR + threadIdx.x]);
+        out[threadIdx.x] = x;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_rounds
+template <typename W>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
+    extern __shared__ uint32_t tbl[];  // W positions
+    __shared__ KMax red[SNW * MAXR];
+    __shared__ KMax res[MAXR];
+    __shared__ unsigned int cge[MAXR + 1];
+    __shared__ int sh_seg;
+    const int tid = threadIdx.x;
+    const uint32_t b = blockIdx.x;
+    const uint32_t s0 = a.bstart[b], s1 = a.bstart[b + 1];
+    const uint32_t nbk = s1 - s0;
+    if (nbk == 0) {
+        if (tid < MAXR) { OKey z; z.k = 0; z.tb = 0; z.valid = 0; a.bmax[(size_t)b * MAXR + tid] = z; }
+        return;
+    }
+    if (tid == 0) sh_seg = seg_of_bucket(a.segs, a.nseg, b);
+    if (tid <= MAXR) cge[tid] = 0;
+    __syncthreads();
+    const Seg &sg = a.segs[sh_seg];
+    const int eps = (int)sg.eps;
+    const uint32_t Wn = 1u << a.wlog, wm = Wn - 1u;
+    const int dt = a.dtype;
+    KMax mx[MAXR];
+    for (int r = 0; r < MAXR; ++r) mx[r] = kmax_none();
+    uint32_t ge[MAXR + 1];
+    for (int r = 0; r <= MAXR; ++r) ge[r] = 0;
+
+    if (nbk <= (uint32_t)ROUND_CAP) {
+        uint16_t ls[ROUND_ITEMS];
+        uint8_t cur[ROUND_ITEMS];
+#pragma unroll
+        for (int k = 0; k < ROUND_ITEMS; ++k) {
+            const uint32_t i = k * SOLVE_THREADS + tid;
+            cur[k] = 0;
+            ls[k] = (i < nbk) ? (uint16_t)(a.gs[s0 + i] & wm) : 0;
+        }
+        for (int r = 0; r < eps; ++r) {
+            for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) tbl[j] = EMPTY32;
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < ROUND_ITEMS; ++k) {
+                const uint32_t i = k * SOLVE_THREADS + tid;
+                if (i < nbk && cur[k] == r) atomicMin(&tbl[ls[k]], i);
+            }
+            __syncthreads();
+            int left = 0;
+#pragma unroll
+            for (int k = 0; k < ROUND_ITEMS; ++k) {
+                const uint32_t i = k * SOLVE_THREADS + tid;
+                if (i < nbk && cur[k] == r && tbl[ls[k]] != i) { cur[k] = (uint8_t)(r + 1); left = 1; }
+            }
+            if (__syncthreads_or(left) == 0) break;
+        }
+#pragma unroll
+        for (int k = 0; k < ROUND_ITEMS; ++k) {
+            const uint32_t i = k * SOLVE_THREADS + tid;
+            if (i < nbk) {
+                const int c = cur[k] > eps ? eps : cur[k];
+                a.rank[s0 + i] = (uint8_t)c;
+                for (int r = 1; r <= eps; ++r) ge[r] += (c >= r);
+                if (c < eps) {
+                    KMax x;
+                    x.k = ordbits(word64(ldk<W>(a.keys, s0 + i)), dt);
+                    x.tb = a.rows ? a.rows[s0 + i] : i;
+                    x.valid = 1;
+                    mx[c] = kmax(mx[c], x);
+                }
+            }
+        }
+    } else {
+        // bucket beyond the register-resident capacity: state lives in the global rank array
+        if (tid == 0) atomicAdd(&a.stats[sh_seg].oversized, 1u);
+        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) a.rank[s0 + i] = 0;
+        __syncthreads();
+        for (int r = 0; r < eps; ++r) {
+            for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) tbl[j] = EMPTY32;
+            __syncthreads();
+            for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS)
+                if (a.rank[s0 + i] == r) atomicMin(&tbl[a.gs[s0 + i] & wm], i);
+            __syncthreads();
+            int left = 0;
+            for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS)
+                if (a.rank[s0 + i] == r && tbl[a.gs[s0 + i] & wm] != i) {
+                    a.rank[s0 + i] = (uint8_t)(r + 1);
+                    left = 1;
+                }
+            if (__syncthreads_or(left) == 0) break;
+        }
+        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) {
+            const int c = a.rank[s0 + i];
+            for (int r = 1; r <= eps; ++r) ge[r] += (c >= r);
+            if (c < eps) {
+                KMax x;
+                x.k = ordbits(word64(ldk<W>(a.keys, s0 + i)), dt);
+                x.tb = a.rows ? a.rows[s0 + i] : i;
+                x.valid = 1;
+                mx[c] = kmax(mx[c], x);
+            }
+        }
+    }
+    // totals
+    for (int r = 1; r <= eps; ++r) {
+        const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, ge[r]);
+        if ((tid & 31) == 0 && v) atomicAdd(&cge[r], v);
+    }
+    block_reduce_kmax_rounds(mx, eps, red, res);
+    if (tid >= 1 && tid <= eps && cge[tid]) atomicAdd(&a.stats[sh_seg].count_ge[tid], (unsigned long long)cge[tid]);
+    if (tid < eps) {
+        OKey o;
+        o.k = res[tid].k; o.tb = res[tid].tb; o.valid = res[tid].valid;
+        a.bmax[(size_t)b * MAXR + tid] = o;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_finalize: one block per array
+__global__ void __launch_bounds__(SOLVE_THREADS) k_finalize(SolveArgs a) {
+    __shared__ KMax scratch[33];
+    __shared__ int sh_t;
+    const int s = blockIdx.x, tid = threadIdx.x;
+    const Seg &sg = a.segs[s];
+    SegStats &st = a.stats[s];
+    if (tid == 0) {
+        uint32_t t = 0;
+        unsigned long long w = sg.n;
+        while (t < sg.eps && w > sg.tau) {
+            ++t;
+            w = st.count_ge[t];
+        }
+        st.count_ge[0] = sg.n;
+        st.t = t;
+        sh_t = (int)t;
+    }
+    __syncthreads();
+    const int t = sh_t;
+    const uint32_t nb = sg.nb, bb = sg.bbase;
+    const uint32_t per = (nb + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    const uint32_t c0 = std::min(nb, tid * per), c1 = std::min(nb, c0 + per);
+    for (int r = 0; r < t; ++r) {
+        KMax loc = kmax_none();
+        for (uint32_t c = c0; c < c1; ++c) {
+            const OKey o = a.bmax[(size_t)(bb + c) * MAXR + r];
+            KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid;
+            loc = kmax(loc, x);
+        }
+        KMax run = block_excl_max(loc, scratch, nullptr);
+        for (uint32_t c = c0; c < c1; ++c) {
+            OKey co; co.k = run.k; co.tb = run.tb; co.valid = run.valid;
+            a.carry[(size_t)(bb + c) * MAXR + r] = co;
+            const OKey o = a.bmax[(size_t)(bb + c) * MAXR + r];
+            KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid;
+            run = kmax(run, x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// CTA-level building blocks on index lists
+
+// stable LSD radix sort of an index list by a 32- or 64-bit digit source, 8 bits per pass,
+// skipping passes whose digit is constant over the list. Returns the buffer holding the result.
+template <typename Idx, typename DigitFn>
+__device__ Idx *cta_radix_sort(Idx *src, Idx *dst, uint32_t cnt, int keybits, DigitFn digit,
+                               uint32_t *hist /*256*/, uint16_t *wcnt /*[SNW][256]*/,
+                               uint32_t *tot /*256*/, uint32_t *scratch /*33*/) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int shift = 0; shift < keybits; shift += 8) {
+        if (tid < 256) hist[tid] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) atomicAdd(&hist[digit(src[i], shift)], 1u);
+        __syncthreads();
+        const bool skip = cnt == 0 || hist[digit(src[0], shift)] == cnt;
+        __syncthreads();
+        if (skip) continue;
+        const uint32_t hv = (tid < 256) ? hist[tid] : 0u;
+        const uint32_t ex = block_excl_sum(hv, scratch, nullptr);
+        if (tid < 256) {
+            hist[tid] = ex;  // running base per digit
+            for (int ww = 0; ww < SNW; ++ww) wcnt[ww * 256 + tid] = 0;
+        }
+        __syncthreads();
+        for (uint32_t t0 = 0; t0 < cnt; t0 += SOLVE_THREADS) {
+            const uint32_t i = t0 + tid;
+            const bool valid = i < cnt;
+            const Idx x = valid ? src[i] : (Idx)0;
+            const uint32_t d = valid ? digit(x, shift) : 0x1FFu;
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+            const uint32_t wr = __popc(peers & lt);
+            if (valid && (peers & lt) == 0) wcnt[w * 256 + d] = (uint16_t)__popc(peers);
+            __syncthreads();
+            if (tid < 256) {
+                uint32_t run = 0;
+                for (int ww = 0; ww < SNW; ++ww) {
+                    const uint32_t c = wcnt[ww * 256 + tid];
+                    wcnt[ww * 256 + tid] = (uint16_t)run;
+                    run += c;
+                }
+                tot[tid] = run;
+            }
+            __syncthreads();
+            if (valid) dst[hist[d] + wcnt[w * 256 + d] + wr] = x;
+            __syncthreads();
+            if (tid < 256) {
+                hist[tid] += tot[tid];
+                for (int ww = 0; ww < SNW; ++ww) wcnt[ww * 256 + tid] = 0;
+            }
+            __syncthreads();
+        }
+        Idx *tmp = src; src = dst; dst = tmp;
+    }
+    return src;
+}
+
+// merge two lists sorted under `less` (a strict total order) into C; caller synchronises
+template <typename Idx, typename Less>
+__device__ void cta_merge(const Idx *A, uint32_t na, const Idx *B, uint32_t nb, Idx *C, Less less) {
+    const uint32_t total = na + nb;
+    const uint32_t per = (total + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    const uint32_t d0 = std::min(total, threadIdx.x * per), d1 = std::min(total, d0 + per);
+    if (d0 >= d1) return;
+    uint32_t lo = d0 > nb ? d0 - nb : 0, hi = std::min(d0, na);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (less(B[d0 - 1 - mid], A[mid])) hi = mid; else lo = mid + 1;
+    }
+    uint32_t i = lo, j = d0 - lo;
+    for (uint32_t q = d0; q < d1; ++q) {
+        if (j >= nb || (i < na && less(A[i], B[j]))) C[q] = A[i++];
+        else C[q] = B[j++];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_polish
+struct PolishSmem {
+    uint32_t hist[256];
+    uint32_t tot[256];
+    uint16_t wcnt[SNW * 256];
+    uint32_t scratch[33];
+    KMax kscratch[33];
+    uint32_t rl_off[MAXR + 1];
+    unsigned int ooo[MAXR];
+    int seg, t;
+};
+
+template <typename W, typename Idx>
+struct BucketView {
+    // element accessors (generic pointers: shared memory on chip, global memory otherwise)
+    const W *K;        // keys
+    const uint16_t *S16;  // on-chip local positions (or null)
+    const uint32_t *G;    // global positions (when S16 is null)
+    const uint8_t *R;     // iteration index
+    uint8_t *F;           // 1: sorted as leftover (last conflict array or out of order)
+    const uint32_t *P;    // payload (nullable)
+    const uint32_t *T;    // rows (nullable)
+    Idx *X, *Y, *RL, *TB;
+    uint32_t wm;
+    int dtype;
+    __device__ __forceinline__ uint32_t ls(uint32_t i) const { return S16 ? S16[i] : (G[i] & wm); }
+    __device__ __forceinline__ unsigned long long ok(uint32_t i) const { return ordbits(word64(K[i]), dtype); }
+    __device__ __forceinline__ uint32_t tb(uint32_t i) const { return T ? T[i] : i; }
+    __device__ __forceinline__ bool less(uint32_t a, uint32_t b) const {
+        const unsigned long long ka = ok(a), kb = ok(b);
+        return ka < kb || (ka == kb && tb(a) < tb(b));
+    }
+};
+
+template <typename W, typename Idx>
+__device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx> &v,
+                              uint32_t b, uint32_t s0, uint32_t nbk, const Seg &sg) {
+    const int tid = threadIdx.x;
+    const int t = sm.t;
+    const uint32_t Wn = v.wm + 1u;
+    const Idx EMPTY = (Idx)~(Idx)0;
+    const int keybits = (a.key_bytes == 4) ? 32 : 64;
+    for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.F[i] = (v.R[i] >= t) ? 1 : 0;
+    if (tid <= MAXR) sm.rl_off[tid] = 0;
+    if (tid < MAXR) sm.ooo[tid] = 0;
+    __syncthreads();
+    uint32_t rl_n = 0;
+    for (int r = 0; r < t; ++r) {
+        // o_r: stored elements in position order
+        for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) v.TB[j] = EMPTY;
+        __syncthreads();
+        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS)
+            if (v.R[i] == r) v.TB[v.ls(i)] = (Idx)i;
+        __syncthreads();
+        const uint32_t per_s = (Wn + SOLVE_THREADS - 1) / SOLVE_THREADS;
+        const uint32_t p0 = std::min(Wn, tid * per_s), p1 = std::min(Wn, p0 + per_s);
+        uint32_t c = 0;
+        for (uint32_t j = p0; j < p1; ++j) c += (v.TB[j] != EMPTY);
+        uint32_t nseq;
+        uint32_t o = block_excl_sum(c, sm.scratch, &nseq);
+        for (uint32_t j = p0; j < p1; ++j)
+            if (v.TB[j] != EMPTY) v.Y[o++] = v.TB[j];
+        __syncthreads();
+        // out-of-order split against the running maximum (carry from earlier buckets first)
+        const uint32_t per = (nseq + SOLVE_THREADS - 1) / SOLVE_THREADS;
+        const uint32_t q0 = std::min(nseq, tid * per), q1 = std::min(nseq, q0 + per);
+        KMax loc = kmax_none();
+        for (uint32_t q = q0; q < q1; ++q) {
+            const uint32_t x = v.Y[q];
+            KMax e; e.k = v.ok(x); e.tb = v.tb(x); e.valid = 1;
+            loc = kmax(loc, e);
+        }
+        KMax run = block_excl_max(loc, sm.kscratch, nullptr);
+        {
+            const OKey cr = a.carry[(size_t)b * MAXR + r];
+            KMax cc; cc.k = cr.k; cc.tb = cr.tb; cc.valid = cr.valid;
+            run = kmax(cc, run);
+        }
+        uint32_t kept = 0, evicted = 0;
+        for (uint32_t q = q0; q < q1; ++q) {
+            const uint32_t x = v.Y[q];
+            const unsigned long long xk = v.ok(x);
+            const uint32_t xt = v.tb(x);
+            if (run.valid && okey_less(xk, xt, run.k, run.tb)) {
+                v.F[x] = 1;
+                ++evicted;
+            } else {
+                run.k = xk; run.tb = xt; run.valid = 1;
+                ++kept;
+            }
+        }
+        if (evicted) atomicAdd(&sm.ooo[r], evicted);
+        uint32_t nkept;
+        uint32_t ko = block_excl_sum(kept, sm.scratch, &nkept);
+        for (uint32_t q = q0; q < q1; ++q) {
+            const uint32_t x = v.Y[q];
+            if (!v.F[x]) v.RL[rl_n + ko++] = (Idx)x;
+        }
+        rl_n += nkept;
+        if (tid == 0) sm.rl_off[r + 1] = rl_n;
+        __syncthreads();
+    }
+    // leftover: the last conflict array and every out-of-order element, in input order
+    const uint32_t per_e = (nbk + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    const uint32_t e0 = std::min(nbk, tid * per_e), e1 = std::min(nbk, e0 + per_e);
+    uint32_t lc = 0;
+    for (uint32_t i = e0; i < e1; ++i) lc += v.F[i];
+    uint32_t nl;
+    uint32_t lo_ = block_excl_sum(lc, sm.scratch, &nl);
+    for (uint32_t i = e0; i < e1; ++i)
+        if (v.F[i]) v.X[lo_++] = (Idx)i;
+    __syncthreads();
+    // QuickSort(w): stable radix sort by key (input order breaks ties, i.e. (key, row) order)
+    auto dig = [&](Idx x, int shift) -> uint32_t { return (uint32_t)((v.ok(x) >> shift) & 0xFFu); };
+    Idx *A = cta_radix_sort<Idx>(v.X, v.Y, nl, keybits, dig, sm.hist, sm.wcnt, sm.tot, sm.scratch);
+    Idx *Bf = (A == v.X) ? v.Y : v.X;
+    __syncthreads();
+    // polish: A' <- merge(A', R_i), i = 1..t
+    uint32_t na = nl;
+    auto lessf = [&](Idx x, Idx y) { return v.less(x, y); };
+    for (int r = 0; r < t; ++r) {
+        const uint32_t r0 = sm.rl_off[r], r1 = sm.rl_off[r + 1];
+        cta_merge<Idx>(A, na, v.RL + r0, r1 - r0, Bf, lessf);
+        __syncthreads();
+        na += r1 - r0;
+        Idx *tmp = A; A = Bf; Bf = tmp;
+    }
+    // write the bucket's sorted run in place of the caller's array
+    const uint64_t off = (uint64_t)s0 - sg.ebase;
+    W *outk = reinterpret_cast<W *>(sg.keys) + off;
+    int32_t *outp = sg.payload ? sg.payload + off : nullptr;
+    for (uint32_t p = tid; p < nbk; p += SOLVE_THREADS) {
+        const uint32_t x = A[p];
+        outk[p] = v.K[x];
+        if (outp) outp[p] = (int32_t)v.P[x];
+        if (a.out_rows) a.out_rows[s0 + p] = v.T[x];
+        if (a.fate) {
+            const int rr = v.R[x];
+            const int8_t f = (rr < t) ? (int8_t)(v.F[x] ? -(rr + 1) : (rr + 1)) : (int8_t)0;
+            a.fate[v.T[x]] = f;
+        }
+    }
+    if (tid < t && sm.ooo[tid]) atomicAdd(&a.stats[sm.seg].ooo[tid], (unsigned long long)sm.ooo[tid]);
+    if (tid == 0) {
+        const uint32_t xf = A[0], xl = A[nbk - 1];
+        OKey lo, hi;
+        lo.k = v.ok(xf); lo.tb = v.T ? v.T[xf] : 0u; lo.valid = 1;
+        hi.k = v.ok(xl); hi.tb = v.T ? v.T[xl] : 0u; hi.valid = 1;
+        a.blo[b] = lo;
+        a.bhi[b] = hi;
+    }
+}
+
+int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks_per_sm,
+                    size_t *smem_bytes) {
+    const size_t fixed = sizeof(PolishSmem) + 256;
+    const size_t tbl = ((size_t)4 << wlog);
+    const size_t per = key_bytes + 2 + 1 + 1 + (payload ? 4 : 0) + (rows ? 4 : 0) + 3 * 2;
+    // shared memory per SM is 228 KB; each resident block also reserves 1 KB
+    const size_t budget = (blocks_per_sm <= 1 ? 226 : 226 / blocks_per_sm - 2) * 1024 - sizeof(PolishSmem);
+    long cap = (long)((budget - fixed - tbl) / per);
+    cap = std::min<long>(cap, 65534);
+    cap &= ~15L;
+    if (smem_bytes) *smem_bytes = fixed + tbl + (size_t)cap * per + 64;
+    return (int)cap;
+}
+
+template <typename W>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
+    extern __shared__ __align__(16) unsigned char praw[];
+    PolishSmem &sm = *reinterpret_cast<PolishSmem *>(praw);
+    unsigned char *dyn = praw + ((sizeof(PolishSmem) + 15) & ~(size_t)15);
+    const int tid = threadIdx.x;
+    const uint32_t b = blockIdx.x;
+    const uint32_t s0 = a.bstart[b], s1 = a.bstart[b + 1];
+    const uint32_t nbk = s1 - s0;
+    if (nbk == 0) return;
+    if (*a.err) return;  // NaN keys / bad positions: leave the caller's arrays untouched
+    if (tid == 0) {
+        sm.seg = seg_of_bucket(a.segs, a.nseg, b);
+        sm.t = (int)a.stats[sm.seg].t;
+    }
+    __syncthreads();
+    const Seg &sg = a.segs[sm.seg];
+    const uint32_t Wn = 1u << a.wlog;
+    const uint32_t cap = (uint32_t)a.polish_cap;
+    if (nbk <= cap) {
+        // on-chip: stage the bucket in shared memory
+        unsigned char *p = dyn;
+        uint32_t *TB = reinterpret_cast<uint32_t *>(p); p += (size_t)4 * Wn;
+        W *K = reinterpret_cast<W *>(p); p += (size_t)sizeof(W) * cap;
+        uint32_t *P = nullptr, *T = nullptr;
+        if (a.pay) { P = reinterpret_cast<uint32_t *>(p); p += (size_t)4 * cap; }
+        if (a.rows) { T = reinterpret_cast<uint32_t *>(p); p += (size_t)4 * cap; }
+        uint16_t *S16 = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
+        uint16_t *X = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
+        uint16_t *Y = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
+        uint16_t *RL = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
+        uint8_t *R = p; p += cap;
+        uint8_t *F = p; p += cap;
+        const W *gk = reinterpret_cast<const W *>(a.keys) + s0;
+        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) {
+            K[i] = gk[i];
+            S16[i] = (uint16_t)(a.gs[s0 + i] & (Wn - 1u));
+            R[i] = a.rank[s0 + i];
+            if (P) P[i] = a.pay[s0 + i];
+            if (T) T[i] = a.rows[s0 + i];
+        }
+        __syncthreads();
+        BucketView<W, uint16_t> v{K, S16, nullptr, R, F, P, T, X, Y, RL,
+                                  reinterpret_cast<uint16_t *>(TB), Wn - 1u, a.dtype};
+        polish_bucket<W, uint16_t>(a, sm, v, b, s0, nbk, sg);
+    } else {
+        uint32_t *TB = reinterpret_cast<uint32_t *>(dyn);
+        BucketView<W, uint32_t> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
+                                  a.rank + s0, a.g_flag + s0, a.pay ? a.pay + s0 : nullptr,
+                                  a.rows ? a.rows + s0 : nullptr, a.g_x + s0, a.g_y + s0,
+                                  a.g_r + s0, TB, Wn - 1u, a.dtype};
+        polish_bucket<W, uint32_t>(a, sm, v, b, s0, nbk, sg);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_seam: one block per array. Locates elements that are smaller than some element of an
+// earlier bucket and re-sorts the smallest range of the output that contains them.
+template <typename W>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_seam(SolveArgs a) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    PolishSmem &sm = *reinterpret_cast<PolishSmem *>(sraw);
+    __shared__ KMax ks[33];
+    __shared__ unsigned long long sh_lo, sh_hi;
+    __shared__ KMax sh_minv;
+    __shared__ int sh_any;
+    const int s = blockIdx.x, tid = threadIdx.x;
+    if (*a.err) return;
+    const Seg &sg = a.segs[s];
+    const int dt = a.dtype;
+    const W *outk = reinterpret_cast<const W *>(sg.keys);
+    const uint32_t nb = sg.nb, bb = sg.bbase;
+    if (tid == 0) { sh_lo = ~0ull; sh_hi = 0; sh_any = 0; sh_minv.valid = 0; }
+    __syncthreads();
+    const uint32_t per = (nb + SOLVE_THREADS - 1) / SOLVE_THREADS;
+    const uint32_t c0 = std::min(nb, tid * per), c1 = std::min(nb, c0 + per);
+    auto nonempty = [&](uint32_t bi) { return a.bstart[bi + 1] > a.bstart[bi]; };
+    auto okey = [&](const OKey &o) { KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid; return x; };
+    KMax loc = kmax_none();
+    for (uint32_t c = c0; c < c1; ++c)
+        if (nonempty(bb + c)) loc = kmax(loc, okey(a.bhi[bb + c]));
+    KMax run = block_excl_max(loc, ks, nullptr);
+    // element order of the output across buckets: by key, then by row when rows are carried
+    auto elem_less_pm = [&](uint64_t pos, const KMax &pm) {
+        const unsigned long long k = ordbits(word64(outk[pos]), dt);
+        const uint32_t tb = a.out_rows ? a.out_rows[sg.ebase + pos] : 0u;
+        return okey_less(k, tb, pm.k, pm.tb);
+    };
+    KMax minv = kmax_none();  // smallest violator (stored as a max with inverted meaning below)
+    unsigned long long hi = 0;
+    bool any = false;
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t bi = bb + c;
+        if (!nonempty(bi)) continue;
+        const KMax lo = okey(a.blo[bi]);
+        if (run.valid && okey_less(lo.k, lo.tb, run.k, run.tb)) {
+            any = true;
+            // violators: the prefix of this bucket's sorted run below the running maximum
+            uint64_t l = a.bstart[bi] - sg.ebase, h = a.bstart[bi + 1] - sg.ebase;
+            while (l < h) {
+                const uint64_t mid = (l + h) >> 1;
+                if (elem_less_pm(mid, run)) l = mid + 1; else h = mid;
+            }
+            hi = std::max<unsigned long long>(hi, l);
+            if (!minv.valid || okey_less(lo.k, lo.tb, minv.k, minv.tb)) minv = lo;
+        }
+        run = kmax(run, okey(a.bhi[bi]));
+    }
+    if (any) {
+        atomicOr(&sh_any, 1);
+        atomicMax(&sh_hi, hi);
+    }
+    __syncthreads();
+    if (!sh_any) return;
+    // global minimum violator (serialised through thread 0 of each warp; rare path)
+    for (int w = 0; w < SOLVE_THREADS / 32; ++w) {
+        if ((tid >> 5) == w) {
+            for (int l = 0; l < 32; ++l) {
+                if ((tid & 31) == l && minv.valid &&
+                    (!sh_minv.valid || okey_less(minv.k, minv.tb, sh_minv.k, sh_minv.tb)))
+                    sh_minv = minv;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        // first output position holding an element greater than the smallest violator
+        const KMax mv = sh_minv;
+        uint32_t bs = bb;
+        for (uint32_t c = 0; c < nb; ++c) {
+            if (!nonempty(bb + c)) continue;
+            const KMax h = okey(a.bhi[bb + c]);
+            if (okey_less(mv.k, mv.tb, h.k, h.tb)) { bs = bb + c; break; }
+        }
+        uint64_t l = a.bstart[bs] - sg.ebase, h = a.bstart[bs + 1] - sg.ebase;
+        while (l < h) {
+            const uint64_t mid = (l + h) >> 1;
+            const unsigned long long k = ordbits(word64(outk[mid]), dt);
+            const uint32_t tb = a.out_rows ? a.out_rows[sg.ebase + mid] : 0u;
+            if (!okey_less(mv.k, mv.tb, k, tb)) l = mid + 1; else h = mid;
+        }
+        sh_lo = l;
+        a.stats[s].repair_lo = l;
+        a.stats[s].repair_hi = sh_hi;
+        a.stats[s].repair_lo_hi_valid = 1;
+        a.stats[s].repaired = sh_hi - l;
+    }
+    __syncthreads();
+    // re-sort [lo, hi) of the output by (key, row): the range is a union of sorted runs
+    const uint64_t lo = sh_lo, len = sh_hi - sh_lo;
+    uint32_t *X = a.g_x + sg.ebase + lo, *Y = a.g_y + sg.ebase + lo;
+    for (uint32_t i = tid; i < len; i += SOLVE_THREADS) X[i] = i;
+    __syncthreads();
+    const W *rk = outk + lo;
+    const uint32_t *rr = a.out_rows ? a.out_rows + sg.ebase + lo : nullptr;
+    uint32_t *res = X;
+    if (rr) {
+        auto rdig = [&](uint32_t x, int shift) -> uint32_t { return (rr[x] >> shift) & 0xFFu; };
+        res = cta_radix_sort<uint32_t>(X, Y, (uint32_t)len, 32, rdig, sm.hist, sm.wcnt, sm.tot, sm.scratch);
+    }
+    uint32_t *oth = (res == X) ? Y : X;
+    auto kdig = [&](uint32_t x, int shift) -> uint32_t {
+        return (uint32_t)((ordbits(word64(rk[x]), dt) >> shift) & 0xFFu);
+    };
+    res = cta_radix_sort<uint32_t>(res, oth, (uint32_t)len, a.key_bytes * 8, kdig, sm.hist, sm.wcnt,
+                                   sm.tot, sm.scratch);
+    __syncthreads();
+    // gather through scratch, then copy back
+    W *tk = reinterpret_cast<W *>(a.key_scratch) + sg.ebase;
+    uint32_t *tp = a.pay_scratch ? a.pay_scratch + sg.ebase : nullptr;
+    uint32_t *tr = a.row_scratch ? a.row_scratch + sg.ebase : nullptr;
+    int32_t *op = sg.payload ? sg.payload + lo : nullptr;
+    for (uint32_t i = tid; i < len; i += SOLVE_THREADS) {
+        const uint32_t x = res[i];
+        tk[i] = rk[x];
+        if (op && tp) tp[i] = (uint32_t)op[x];
+        if (rr && tr) tr[i] = rr[x];
+    }
+    __syncthreads();
+    W *wk = reinterpret_cast<W *>(sg.keys) + lo;
+    for (uint32_t i = tid; i < len; i += SOLVE_THREADS) {
+        wk[i] = tk[i];
+        if (op && tp) op[i] = (int32_t)tp[i];
+        if (rr && tr) a.out_rows[sg.ebase + lo + i] = tr[i];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+template <typename W> static cudaError_t rounds_go(const SolveArgs &a, cudaStream_t s) {
+    const size_t smem = (size_t)4 << a.wlog;
+    cudaError_t e = cudaFuncSetAttribute(k_rounds<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_rounds<W><<<a.NB, SOLVE_THREADS, smem, s>>>(a);
+    return nns_launched(cudaGetLastError());
+}
+cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s) {
+    if (a.NB == 0) return cudaSuccess;
+    return a.key_bytes == 4 ? rounds_go<uint32_t>(a, s) : rounds_go<uint64_t>(a, s);
+}
+
+cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s) {
+    k_finalize<<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
+    return nns_launched(cudaGetLastError());
+}
+
+template <typename W> static cudaError_t polish_go(const SolveArgs &a, cudaStream_t s) {
+    const size_t smem = std::max(a.polish_smem, sizeof(PolishSmem) + 16 + ((size_t)4 << a.wlog));
+    cudaError_t e = cudaFuncSetAttribute(k_polish<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_polish<W><<<a.NB, SOLVE_THREADS, smem, s>>>(a);
+    return nns_launched(cudaGetLastError());
+}
+cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s) {
+    if (a.NB == 0) return cudaSuccess;
+    return a.key_bytes == 4 ? polish_go<uint32_t>(a, s) : polish_go<uint64_t>(a, s);
+}
+
+template <typename W> static cudaError_t seam_go(const SolveArgs &a, cudaStream_t s) {
+    const size_t smem = sizeof(PolishSmem);
+    k_seam<W><<<a.nseg, SOLVE_THREADS, smem, s>>>(a);
+    return nns_launched(cudaGetLastError());
+}
+cudaError_t launch_seam_repair(const SolveArgs &a, cudaStream_t s) {
+    return a.key_bytes == 4 ? seam_go<uint32_t>(a, s) : seam_go<uint64_t>(a, s);
+}
+
+}  // namespace nns

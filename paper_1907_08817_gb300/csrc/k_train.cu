@@ -1,0 +1,405 @@
+// k_train.cu -- training the model f on the device (Sec. "Training"; Sec. "Experimental Study /
+// Training details"; Eq. (loss)).
+//
+//   * sampling: S draws with replacement from the SplitMix64 stream of the training seed;
+//   * labels: after a stable radix sort of the sample, label_j = j / S (the empirical CDF);
+//   * gradient: each block takes a fixed chunk of the batch, runs the binary32 forward pass,
+//     the loss derivative and backpropagation per sample, and reduces the chunk's parameter
+//     gradient as small matrix products over its samples in a fixed order (no atomics);
+//     block partials are then summed in block order, so gradients are reproducible;
+//   * Adam (Kingma & Ba), bias-corrected, in binary32.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nns {
+static inline cudaError_t nns_launched(cudaError_t e, int k = 1) {
+    if (e == cudaSuccess) note_launch(k);
+    return e;
+}
+}  // namespace nns
+
+namespace nns {
+
+constexpr int TR_THREADS = 256;
+constexpr int TR_CHUNK = 64;  // samples whose activations a block stages at once
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t rng_draw(uint64_t seed, uint64_t i) {
+    return mix64(seed + (i + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+// ---- sampling
+template <typename W>
+__global__ void k_sample(const W *keys, uint64_t n, int dtype, uint64_t S, uint64_t seed, W *out,
+                         uint32_t *rows, uint32_t *err) {
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = __umul64hi(rng_draw(seed, j), n);
+        const W k = keys[r];
+        if (key_is_nan(word64(k), dtype)) atomicOr(err, ERR_NAN);
+        out[j] = k;
+        rows[j] = (uint32_t)r;
+    }
+}
+
+cudaError_t launch_sample(const void *keys, uint64_t n, int key_bytes, int dtype, uint64_t S,
+                          uint64_t stream_seed, void *sample_keys, uint32_t *sample_rows,
+                          uint32_t *err, cudaStream_t s) {
+    const int grid = (int)std::min<uint64_t>((S + 255) / 256, 4096);
+    if (key_bytes == 4)
+        k_sample<uint32_t><<<grid, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(keys), n, dtype, S,
+                                                stream_seed, reinterpret_cast<uint32_t *>(sample_keys),
+                                                sample_rows, err);
+    else
+        k_sample<uint64_t><<<grid, 256, 0, s>>>(reinterpret_cast<const uint64_t *>(keys), n, dtype, S,
+                                                stream_seed, reinterpret_cast<uint64_t *>(sample_keys),
+                                                sample_rows, err);
+    return nns_launched(cudaGetLastError());
+}
+
+template <typename W>
+__global__ void k_make_xy(const W *sorted, uint64_t S, const Norm *nm, float *x, float *label) {
+    const Norm N = *nm;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        x[j] = translate_x(word64(sorted[j]), N);
+        label[j] = __double2float_rn(__ddiv_rn((double)j, (double)S));
+    }
+}
+
+cudaError_t launch_make_xy(const void *sorted_keys, uint64_t S, int key_bytes, const Norm *nm_dev,
+                           float *x, float *label, cudaStream_t s) {
+    const int grid = (int)std::min<uint64_t>((S + 255) / 256, 4096);
+    if (key_bytes == 4)
+        k_make_xy<uint32_t><<<grid, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(sorted_keys), S,
+                                                 nm_dev, x, label);
+    else
+        k_make_xy<uint64_t><<<grid, 256, 0, s>>>(reinterpret_cast<const uint64_t *>(sorted_keys), S,
+                                                 nm_dev, x, label);
+    return nns_launched(cudaGetLastError());
+}
+
+// ---- forward pass for explicit inputs
+template <int H1, int H2>
+__global__ void k_mlp_forward(const float *params, const float *x, uint64_t n, float *y) {
+    extern __shared__ __align__(16) float sp[];
+    constexpr int P = (H2 == 0) ? (3 * H1 + 1) : (2 * H1 + H2 * H1 + 2 * H2 + 1);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sp[i] = params[i];
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        y[i] = mlp_fwd_f32<H1, H2>(sp, x[i]);
+}
+
+// ---- gradient of a sum over samples
+// mode 0: s = sum_i gy_i * y_i (explicit upstream gradient); mode 1: mean loss over the batch
+// with labels; mode 2: as mode 1 with batch indices drawn from the batch stream.
+struct GradArgs {
+    const float *params;
+    const float *x, *gy, *label;
+    uint64_t n;          // samples in the batch
+    uint64_t S;          // labelled set size (mode 2)
+    uint64_t bseed;      // batch stream (mode 2)
+    uint64_t bofs;       // first draw of this step (mode 2)
+    int mode, loss;
+    float delta;
+    float inv_n;
+    float *partials;     // [gridDim.x * P]
+    float *loss_partials;  // [gridDim.x]
+    float *gx;           // nullable (mode 0)
+};
+
+template <int H1, int H2>
+__global__ void __launch_bounds__(TR_THREADS) k_grad(GradArgs g) {
+    constexpr int HL = (H2 == 0) ? H1 : H2;
+    constexpr int P = (H2 == 0) ? (3 * H1 + 1) : (2 * H1 + H2 * H1 + 2 * H2 + 1);
+    extern __shared__ __align__(16) float sm[];
+    float *sp = sm;                               // parameters (P, padded to 4)
+    float *sx = sp + ((P + 3) & ~3);              // [CH] inputs
+    float *sgy = sx + TR_CHUNK;                   // [CH] dL/dy
+    float *sh1 = sgy + TR_CHUNK;                  // [CH][H1] hidden 1 activations
+    float *sd1 = sh1 + TR_CHUNK * H1;             // [CH][H1] delta at hidden-1 pre-activations
+    float *sh2 = sd1 + TR_CHUNK * H1;             // [CH][H2]
+    float *sd2 = sh2 + TR_CHUNK * (H2 ? H2 : 1);  // [CH][H2]
+    float *sloss = sd2 + TR_CHUNK * (H2 ? H2 : 1);  // [CH]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < P; i += blockDim.x) sp[i] = g.params[i];
+    __syncthreads();
+    const float *W1 = sp, *b1 = sp + H1;
+    const float *W2 = sp + 2 * H1, *b2 = W2 + H2 * H1;
+    const float *W3 = (H2 == 0) ? sp + 2 * H1 : b2 + H2;
+    // each block owns a contiguous range of the batch
+    const uint64_t per = (g.n + gridDim.x - 1) / gridDim.x;
+    const uint64_t i0 = std::min<uint64_t>(g.n, (uint64_t)blockIdx.x * per);
+    const uint64_t i1 = std::min<uint64_t>(g.n, i0 + per);
+    float acc[(P + TR_THREADS - 1) / TR_THREADS];
+#pragma unroll
+    for (int q = 0; q < (P + TR_THREADS - 1) / TR_THREADS; ++q) acc[q] = 0.0f;
+    float lacc = 0.0f;
+    for (uint64_t c0 = i0; c0 < i1; c0 += TR_CHUNK) {
+        const int cn = (int)std::min<uint64_t>(TR_CHUNK, i1 - c0);
+        // phase A: one sample per thread (threads >= cn idle)
+        if (tid < cn) {
+            const uint64_t i = c0 + tid;
+            uint64_t src = i;
+            if (g.mode == 2) src = __umul64hi(rng_draw(g.bseed, g.bofs + i), g.S);
+            const float x = g.x[src];
+            float h1[H1];
+#pragma unroll
+            for (int j = 0; j < H1; ++j) h1[j] = relu_f(__fmaf_rn(W1[j], x, b1[j]));
+            float y;
+            if constexpr (H2 == 0) {
+                y = W3[H1];
+#pragma unroll
+                for (int k = 0; k < H1; ++k) y = __fmaf_rn(W3[k], h1[k], y);
+            } else {
+                y = W3[H2];
+                for (int k = 0; k < H2; ++k) {
+                    float z = b2[k];
+#pragma unroll
+                    for (int j = 0; j < H1; ++j) z = __fmaf_rn(W2[k * H1 + j], h1[j], z);
+                    sd2[tid * H2 + k] = z;  // pre-activation, replaced by its delta below
+                    const float h = relu_f(z);
+                    sh2[tid * H2 + k] = h;
+                    y = __fmaf_rn(W3[k], h, y);
+                }
+            }
+            float gy, lv = 0.0f;
+            if (g.mode == 0) {
+                gy = g.gy[i];
+            } else {
+                const float r = y - g.label[src];
+                if (g.loss == NNSORT_LOSS_HUBER) {
+                    const float ar = fabsf(r);
+                    lv = (ar <= g.delta) ? 0.5f * r * r : g.delta * ar - 0.5f * g.delta * g.delta;
+                    gy = (r > g.delta) ? g.delta : ((r < -g.delta) ? -g.delta : r);
+                } else {
+                    lv = r * r;
+                    gy = 2.0f * r;
+                }
+                gy *= g.inv_n;
+            }
+            sx[tid] = x;
+            sgy[tid] = gy;
+            sloss[tid] = lv;
+            float d1[H1];
+            if constexpr (H2 == 0) {
+#pragma unroll
+                for (int j = 0; j < H1; ++j) d1[j] = (h1[j] > 0.0f) ? gy * W3[j] : 0.0f;
+            } else {
+#pragma unroll
+                for (int j = 0; j < H1; ++j) d1[j] = 0.0f;
+                for (int k = 0; k < H2; ++k) {
+                    const float d2 = (sd2[tid * H2 + k] > 0.0f) ? gy * W3[k] : 0.0f;
+                    sd2[tid * H2 + k] = d2;
+#pragma unroll
+                    for (int j = 0; j < H1; ++j) d1[j] = __fmaf_rn(d2, W2[k * H1 + j], d1[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < H1; ++j) d1[j] = (h1[j] > 0.0f) ? d1[j] : 0.0f;
+            }
+            float gx = 0.0f;
+#pragma unroll
+            for (int j = 0; j < H1; ++j) {
+                sh1[tid * H1 + j] = h1[j];
+                sd1[tid * H1 + j] = d1[j];
+                gx = __fmaf_rn(d1[j], W1[j], gx);
+            }
+            if (g.gx) g.gx[i] = gx;
+        }
+        __syncthreads();
+        // phase B: every parameter sums its chunk contributions in sample order
+#pragma unroll
+        for (int q = 0; q < (P + TR_THREADS - 1) / TR_THREADS; ++q) {
+            const int p = q * TR_THREADS + tid;
+            if (p >= P) break;
+            float s = 0.0f;
+            if (p < H1) {                                  // W1_j: d1_j * x
+                for (int c = 0; c < cn; ++c) s = __fmaf_rn(sd1[c * H1 + p], sx[c], s);
+            } else if (p < 2 * H1) {                       // b1_j: d1_j
+                const int j = p - H1;
+                for (int c = 0; c < cn; ++c) s = __fadd_rn(s, sd1[c * H1 + j]);
+            } else if (H2 != 0 && p < 2 * H1 + H2 * H1) {  // W2_kj: d2_k * h1_j
+                const int kj = p - 2 * H1, k = kj / (H1 ? H1 : 1), j = kj - k * H1;
+                for (int c = 0; c < cn; ++c) s = __fmaf_rn(sd2[c * (H2 ? H2 : 1) + k], sh1[c * H1 + j], s);
+            } else if (H2 != 0 && p < 2 * H1 + H2 * H1 + H2) {  // b2_k: d2_k
+                const int k = p - 2 * H1 - H2 * H1;
+                for (int c = 0; c < cn; ++c) s = __fadd_rn(s, sd2[c * (H2 ? H2 : 1) + k]);
+            } else if (p < P - 1) {                        // W3_k: gy * h_k
+                const int k = p - (P - 1 - HL);
+                if constexpr (H2 == 0)
+                    for (int c = 0; c < cn; ++c) s = __fmaf_rn(sgy[c], sh1[c * H1 + k], s);
+                else
+                    for (int c = 0; c < cn; ++c) s = __fmaf_rn(sgy[c], sh2[c * (H2 ? H2 : 1) + k], s);
+            } else {                                       // b3: gy
+                for (int c = 0; c < cn; ++c) s = __fadd_rn(s, sgy[c]);
+            }
+            acc[q] = __fadd_rn(acc[q], s);
+        }
+        if (tid == 0)
+            for (int c = 0; c < cn; ++c) lacc = __fadd_rn(lacc, sloss[c]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < (P + TR_THREADS - 1) / TR_THREADS; ++q) {
+        const int p = q * TR_THREADS + tid;
+        if (p < P) g.partials[(size_t)blockIdx.x * P + p] = acc[q];
+    }
+    if (tid == 0 && g.loss_partials) g.loss_partials[blockIdx.x] = lacc;
+}
+
+template <int H1, int H2> static size_t grad_smem() {
+    constexpr int P = (H2 == 0) ? (3 * H1 + 1) : (2 * H1 + H2 * H1 + 2 * H2 + 1);
+    constexpr int H2e = H2 ? H2 : 1;
+    return sizeof(float) * (((P + 3) & ~3) + TR_CHUNK * (3 + 2 * H1 + 2 * H2e));
+}
+
+int train_grad_blocks(uint64_t nsamples) {
+    // at least one chunk per block; at most 1024 blocks
+    const uint64_t b = (nsamples + 4 * TR_CHUNK - 1) / (4 * TR_CHUNK);
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, 1024));
+}
+
+template <int H1, int H2>
+static cudaError_t grad_go(const GradArgs &g, int blocks, cudaStream_t s) {
+    const size_t smem = grad_smem<H1, H2>();
+    cudaError_t e = cudaFuncSetAttribute(k_grad<H1, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_grad<H1, H2><<<blocks, TR_THREADS, smem, s>>>(g);
+    return nns_launched(cudaGetLastError());
+}
+
+static cudaError_t grad_dispatch(const PadArch &a, const GradArgs &g, int blocks, cudaStream_t s) {
+    if (a.layers == 1) {
+        switch (a.h1) {
+        case 8: return grad_go<8, 0>(g, blocks, s);
+        case 16: return grad_go<16, 0>(g, blocks, s);
+        case 32: return grad_go<32, 0>(g, blocks, s);
+        case 64: return grad_go<64, 0>(g, blocks, s);
+        }
+    } else {
+        switch (a.h1) {
+        case 8: return grad_go<8, 8>(g, blocks, s);
+        case 16: return grad_go<16, 16>(g, blocks, s);
+        case 32: return grad_go<32, 32>(g, blocks, s);
+        case 64: return grad_go<64, 64>(g, blocks, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---- fixed-order reduction of block partials (+ optional Adam step)
+struct ReduceArgs {
+    const float *partials;
+    int blocks;
+    size_t P;
+    float *out;                 // gradient (nullable when Adam consumes it directly)
+    const float *loss_partials;
+    float *loss_out;
+    float loss_scale;
+    // Adam
+    float *params, *m, *v;
+    float lr, b1, b2, eps, c1, c2;
+};
+
+__global__ void k_reduce(ReduceArgs r) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0 && r.loss_partials && r.loss_out) {
+        float l = 0.0f;
+        for (int b = 0; b < r.blocks; ++b) l = __fadd_rn(l, r.loss_partials[b]);
+        *r.loss_out = l * r.loss_scale;
+    }
+    if (p >= r.P) return;
+    float g = 0.0f;
+    for (int b = 0; b < r.blocks; ++b) g = __fadd_rn(g, r.partials[(size_t)b * r.P + p]);
+    if (r.out) r.out[p] = g;
+    if (r.params) {
+        const float m = r.b1 * r.m[p] + (1.0f - r.b1) * g;
+        const float v = r.b2 * r.v[p] + (1.0f - r.b2) * g * g;
+        r.m[p] = m;
+        r.v[p] = v;
+        const float mh = m / r.c1, vh = v / r.c2;
+        r.params[p] -= r.lr * mh / (sqrtf(vh) + r.eps);
+    }
+}
+
+cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, float *out,
+                                   const float *loss_partials, float *loss_out, float scale,
+                                   cudaStream_t s) {
+    ReduceArgs r{};
+    r.partials = partials; r.blocks = blocks; r.P = P; r.out = out;
+    r.loss_partials = loss_partials; r.loss_out = loss_out; r.loss_scale = scale;
+    k_reduce<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(r);
+    return nns_launched(cudaGetLastError());
+}
+
+cudaError_t launch_train_step(const PadArch &a, const TrainStepArgs &t, cudaStream_t s) {
+    const uint64_t B = t.batch ? t.batch : t.S;
+    const int blocks = train_grad_blocks(B);
+    GradArgs g{};
+    g.params = t.params; g.x = t.x; g.label = t.label; g.n = B; g.S = t.S;
+    g.bseed = t.batch_seed; g.bofs = (uint64_t)t.step * B;
+    g.mode = t.batch ? 2 : 1; g.loss = t.loss; g.delta = t.delta; g.inv_n = 1.0f / (float)B;
+    g.partials = t.partials; g.loss_partials = t.loss_partials; g.gx = nullptr;
+    cudaError_t e = grad_dispatch(a, g, blocks, s);
+    if (e != cudaSuccess) return e;
+    ReduceArgs r{};
+    r.partials = t.partials; r.blocks = blocks; r.P = t.P; r.out = t.grad;
+    r.loss_partials = t.loss_partials; r.loss_out = t.loss_out + t.step; r.loss_scale = 1.0f / (float)B;
+    r.params = t.params; r.m = t.m; r.v = t.v; r.lr = t.lr; r.b1 = t.b1; r.b2 = t.b2; r.eps = t.eps;
+    const double c1 = 1.0 - std::pow((double)t.b1, (double)(t.step + 1));
+    const double c2 = 1.0 - std::pow((double)t.b2, (double)(t.step + 1));
+    r.c1 = (float)c1; r.c2 = (float)c2;
+    k_reduce<<<(unsigned)((t.P + 255) / 256), 256, 0, s>>>(r);
+    return nns_launched(cudaGetLastError());
+}
+
+cudaError_t launch_mlp_forward(const PadArch &a, const float *params, const float *x, uint64_t n,
+                               float *y, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, 2048);
+#define NNS_F(A, B)                                                                             \
+    {                                                                                           \
+        constexpr int P = (B == 0) ? (3 * A + 1) : (2 * A + B * A + 2 * B + 1);                 \
+        k_mlp_forward<A, B><<<grid, 256, ((P + 3) / 4) * 16, s>>>(params, x, n, y);            \
+        return nns_launched(cudaGetLastError());                                                              \
+    }
+    if (a.layers == 1) {
+        switch (a.h1) {
+        case 8: NNS_F(8, 0)
+        case 16: NNS_F(16, 0)
+        case 32: NNS_F(32, 0)
+        case 64: NNS_F(64, 0)
+        }
+    } else {
+        switch (a.h1) {
+        case 8: NNS_F(8, 8)
+        case 16: NNS_F(16, 16)
+        case 32: NNS_F(32, 32)
+        case 64: NNS_F(64, 64)
+        }
+    }
+#undef NNS_F
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mlp_backward(const PadArch &a, const float *params, const float *x,
+                                const float *gy, const float *label, uint64_t n, int mode,
+                                int loss, float delta, float *partials, float *loss_partials,
+                                float *gx, cudaStream_t s, int *blocks_out) {
+    const int blocks = train_grad_blocks(n);
+    if (blocks_out) *blocks_out = blocks;
+    GradArgs g{};
+    g.params = params; g.x = x; g.gy = gy; g.label = label; g.n = n; g.S = n;
+    g.mode = mode; g.loss = loss; g.delta = delta; g.inv_n = n ? 1.0f / (float)n : 0.0f;
+    g.partials = partials; g.loss_partials = loss_partials; g.gx = gx;
+    return grad_dispatch(a, g, blocks, s);
+}
+
+}  // namespace nns

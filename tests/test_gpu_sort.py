@@ -1,0 +1,232 @@
+"""GPU parity of the NN-sort pipeline against the CPU oracle, through the C ABI.
+
+Positions, outputs, per-iteration counts and per-row fates are integer results and must match the
+oracle bit for bit; the sort output is the stable order of the keys, bit for bit."""
+import numpy as np
+import pytest
+
+from helpers import bits, from_dev, lib_model, oracle_model, stats_core, to_dev
+from oracle import oracle as orc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+import paper_1907_08817_gb300 as nns  # noqa: E402
+
+
+def _rand_model(dtype_code, keys, layers, h1, h2, translate, seed=0, S=2000):
+    rows, nm, _, _ = orc.sample_labels(keys, S, seed, translate)
+    return orc.Model(layers, h1, h2, nm, orc.init_params(layers, h1, h2, seed))
+
+
+def _trained(keys, layers, h1, h2, translate, S=2000, steps=100, seed=0):
+    m, _, _ = orc.train(keys, layers, h1, h2, translate, sample_n=S, steps=steps, lr=1e-2, seed=seed)
+    return m
+
+
+# ---------------------------------------------------------------------------- prediction (a3, a4)
+@pytest.mark.parametrize("case", ["u_f32_value", "ln_f32_ordbits_2l", "gm_u64", "n_f64_value",
+                                  "ln_f32_64x64"])
+def test_predict_positions_bit_exact(case):
+    if case == "u_f32_value":
+        keys, om = W.uniform_f32(100_003, 1), None
+        om = _trained(keys, 1, 32, 0, orc.VALUE)
+    elif case == "ln_f32_ordbits_2l":
+        keys = W.lognormal_dup_f32(77_777, 2, sigma=2.0)
+        om = _trained(keys, 2, 16, 16, orc.ORDBITS, steps=50)
+    elif case == "gm_u64":
+        keys, _ = W.gauss_mix_u64(50_001, 3)
+        om = _trained(keys, 2, 32, 32, orc.ORDBITS, steps=30)
+    elif case == "n_f64_value":
+        keys = W.normal_f32(40_000, 4).astype(np.float64) * 1e3
+        om = _trained(keys, 1, 8, 0, orc.VALUE)
+    else:
+        keys = W.lognormal_dup_f32(20_000, 5, sigma=2.0)
+        om = _rand_model(orc.F32, keys, 2, 64, 64, orc.ORDBITS)
+    f = lib_model(om)
+    dk, kt = to_dev(keys)
+    for m in (1.25, 2.0):
+        slots, y = nns.predict(dk, f, m=m, key_type=kt)
+        om_slots, om_y = orc.predict_slots(keys, om, m)
+        np.testing.assert_array_equal(slots.cpu().numpy().astype(np.uint32), om_slots)
+        np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), om_y.view(np.uint32))
+
+
+# ---------------------------------------------------------------------------- injected positions
+def _check_injected(keys, slots, L, eps, tau, payload=None, bucket_log2=0):
+    dk, kt = to_dev(keys)
+    dp = None if payload is None else torch.from_numpy(payload).cuda()
+    ds = torch.from_numpy(slots.astype(np.uint32).view(np.int32)).cuda()
+    st, fate = nns.sort(dk, dp, None, eps=eps, tau=tau, slots=ds, fate=True, key_type=kt,
+                        bucket_log2=bucket_log2)
+    ok, op, ost, ofate = orc.nnsort(keys, slots, L, eps, tau, payload, want_fate=True)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    if payload is not None:
+        np.testing.assert_array_equal(dp.cpu().numpy(), op)
+    assert stats_core(st) == stats_core(ost)
+    np.testing.assert_array_equal(fate.cpu().numpy(), ofate)
+    return st
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 1023, 4097, 65_537, 300_001])
+def test_injected_positions_match_oracle(n):
+    rs = np.random.RandomState(n)
+    keys = W.normal_f32(n, n)
+    L, _, _ = orc.nm_split(n)
+    # positions roughly following the key order, with noise, collisions and out-of-order picks
+    rank = np.argsort(np.argsort(keys, kind="stable"), kind="stable")
+    slots = np.clip((rank * 1.25 + rs.randint(-3, 4, n)).astype(np.int64), 0, L - 1)
+    slots[rs.rand(n) < 0.05] = rs.randint(0, L, max(1, int((rs.rand(n) < 0.05).sum())))[:1]
+    for eps, tau in ((3, 0), (1, 0), (4, 7), (3, n + 1)):
+        _check_injected(keys, slots.astype(np.uint32), L, eps, tau,
+                        payload=np.arange(n, dtype=np.int32))
+
+
+def test_injected_degenerate_maps():
+    n = 20_000
+    keys = W.uniform_f32(n, 9)
+    L, _, _ = orc.nm_split(n)
+    # every key on one position: each round stores one element, the rest is the leftover
+    st = _check_injected(keys, np.full(n, 5, np.uint32), L, 3, 0, np.arange(n, dtype=np.int32))
+    assert st["w_size"] == [n, n - 1, n - 2, n - 3]
+    # reverse order: every stored element but the first of each o_i is out of order
+    rank = np.argsort(np.argsort(keys, kind="stable"), kind="stable")
+    _check_injected(keys, ((n - 1 - rank) * 5 // 4).astype(np.uint32), L, 3, 0)
+    # random positions over the whole range (non-monotone everywhere: seam repair)
+    rs = np.random.RandomState(3)
+    _check_injected(keys, rs.randint(0, L, n).astype(np.uint32), L, 3, 10,
+                    np.arange(n, dtype=np.int32))
+
+
+def test_injected_small_buckets_and_oversized():
+    rs = np.random.RandomState(11)
+    n = 120_000
+    keys = W.lognormal_f32(n, 12, sigma=1.0)
+    L, _, _ = orc.nm_split(n)
+    rank = np.argsort(np.argsort(keys, kind="stable"), kind="stable")
+    slots = (rank * 5 // 4).astype(np.int64)
+    # a crowded stretch: 40% of the keys squeezed into 64 positions -> oversized buckets
+    crowd = rs.rand(n) < 0.4
+    slots[crowd] = 1000 + (slots[crowd] % 64)
+    st = _check_injected(keys, slots.astype(np.uint32), L, 3, 0, np.arange(n, dtype=np.int32),
+                         bucket_log2=9)
+    assert st["oversized_buckets"] >= 1
+
+
+# ---------------------------------------------------------------------------- model-driven sorts
+@pytest.mark.parametrize("case", ["c1_uniform", "lognormal_dup", "u64_kv", "f64", "two_layer"])
+def test_model_sort_matches_oracle(case):
+    payload = None
+    if case == "c1_uniform":
+        keys = W.uniform_f32(1_000_000, 0)
+        om = _trained(keys, 1, 32, 0, orc.VALUE, S=10_000)
+    elif case == "lognormal_dup":
+        keys = W.lognormal_dup_f32(500_000, 2, sigma=2.0)
+        om = _trained(keys, 1, 32, 0, orc.ORDBITS, S=5000)
+    elif case == "u64_kv":
+        keys, payload = W.gauss_mix_u64(300_000, 3)
+        om = _trained(keys, 2, 16, 16, orc.ORDBITS, S=5000, steps=60)
+    elif case == "f64":
+        keys = W.normal_f32(200_000, 6).astype(np.float64)
+        om = _trained(keys, 1, 16, 0, orc.VALUE, S=3000)
+    else:
+        keys = W.exponential_f32(250_000, 7)
+        om = _trained(keys, 2, 8, 8, orc.ORDBITS, S=3000, steps=80)
+    f = lib_model(om)
+    dk, kt = to_dev(keys)
+    dp = None if payload is None else torch.from_numpy(payload).cuda()
+    st, fate = nns.sort(dk, dp, f, fate=True, key_type=kt)
+    ok, op, ost, ofate = orc.nnsort_model(keys, om, payload=payload, want_fate=True)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    if payload is not None:
+        np.testing.assert_array_equal(dp.cpu().numpy(), op)
+    assert stats_core(st) == stats_core(ost)
+    np.testing.assert_array_equal(fate.cpu().numpy(), ofate)
+    # and without the trace (rows not carried): same output and counts
+    dk2, _ = to_dev(keys)
+    st2 = nns.sort(dk2, None, f, key_type=kt)
+    np.testing.assert_array_equal(bits(from_dev(dk2, keys)), bits(ok))
+    assert stats_core(st2) == stats_core(ost)
+
+
+def test_edge_keys_and_empty():
+    v = np.array([np.inf, -0.0, 0.0, -np.inf, 1.0, -1.0, 0.0, -0.0, 3e38, -3e38, 1e-45, -1e-45] * 50,
+                 dtype=np.float32)
+    rs = np.random.RandomState(0)
+    v = v[rs.permutation(v.shape[0])]
+    om = _rand_model(orc.F32, v, 1, 8, 0, orc.ORDBITS, S=100)
+    f = lib_model(om)
+    dk, _ = to_dev(v)
+    dp = torch.arange(v.shape[0], dtype=torch.int32, device="cuda")
+    st = nns.sort(dk, dp, f)
+    ok, op, ost, _ = orc.nnsort_model(v, om, payload=np.arange(v.shape[0], dtype=np.int32))
+    np.testing.assert_array_equal(bits(from_dev(dk, v)), bits(ok))
+    np.testing.assert_array_equal(dp.cpu().numpy(), op)
+    assert stats_core(st) == stats_core(ost)
+    # all-equal keys
+    eq = np.full(70_000, 2.5, dtype=np.float32)
+    om2 = _rand_model(orc.F32, eq, 1, 8, 0, orc.VALUE, S=100)
+    dk, _ = to_dev(eq)
+    dp = torch.arange(eq.shape[0], dtype=torch.int32, device="cuda")
+    st = nns.sort(dk, dp, lib_model(om2))
+    assert np.array_equal(dp.cpu().numpy(), np.arange(eq.shape[0]))
+    # empty and single
+    e = torch.empty(0, dtype=torch.float32, device="cuda")
+    assert nns.sort(e, None, f)["n"] == 0
+    one = torch.tensor([4.0], device="cuda")
+    nns.sort(one, None, f)
+    assert one.item() == 4.0
+
+
+def test_nan_keys_rejected_input_untouched():
+    keys = W.uniform_f32(10_000, 3)
+    om = _rand_model(orc.F32, keys, 1, 8, 0, orc.VALUE, S=100)
+    keys[777] = np.nan
+    dk, _ = to_dev(keys)
+    before = dk.clone()
+    with pytest.raises(nns.NNSortError) as ei:
+        nns.sort(dk, None, lib_model(om))
+    assert ei.value.status == -2
+    assert torch.equal(dk.view(torch.int32), before.view(torch.int32))
+
+
+def test_invalid_arguments():
+    keys = torch.rand(100, device="cuda")
+    with pytest.raises(nns.NNSortError):
+        nns.sort(keys, None, None)  # no model and no injected positions
+    om = _rand_model(orc.F32, keys.cpu().numpy(), 1, 8, 0, orc.VALUE, S=50)
+    with pytest.raises(nns.NNSortError):
+        nns.sort(keys, None, lib_model(om), eps=99)
+    with pytest.raises(nns.NNSortError):
+        nns.sort(keys.double(), None, lib_model(om))  # dtype differs from the model's
+
+
+# ---------------------------------------------------------------------------- batch
+def test_batch_equals_individual_sorts():
+    arrs, models, oms = [], [], []
+    for j, (kind, a) in enumerate(W.batch_arrays(24, seed=4, lo=1000, hi=200_000)):
+        om = _trained(a, 1, 16, 0, orc.ORDBITS, S=max(100, a.shape[0] // 100), steps=50, seed=j)
+        arrs.append(a)
+        oms.append(om)
+        models.append(lib_model(om))
+    dks = [to_dev(a)[0] for a in arrs]
+    sts = nns.sort_batch(dks, models)
+    for a, om, dk, st in zip(arrs, oms, dks, sts):
+        ok, _, ost, _ = orc.nnsort_model(a, om)
+        np.testing.assert_array_equal(bits(from_dev(dk, a)), bits(ok))
+        assert stats_core(st) == stats_core(ost)
+
+
+def test_host_entry_point():
+    keys = W.lognormal_dup_f32(100_000, 8, sigma=2.0)
+    payload = np.arange(keys.shape[0], dtype=np.int32)
+    om = _trained(keys, 1, 32, 0, orc.ORDBITS, S=1000)
+    k2, p2 = keys.copy(), payload.copy()
+    st = nns.sort_host(k2, p2, lib_model(om))
+    ok, op, ost, _ = orc.nnsort_model(keys, om, payload=payload)
+    np.testing.assert_array_equal(bits(k2), bits(ok))
+    np.testing.assert_array_equal(p2, op)
+    assert stats_core(st) == stats_core(ost)
