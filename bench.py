@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: NN-sort on one GB300 (or N independent replicas under torchrun).
+
+Workload (the large single-GPU configuration): 268,435,456 float32 keys, lognormal(0, 2) with 5%
+exact duplicates, shuffled, keys only; model f = MLP 1 -> 64 -> 64 -> 1 trained on the device
+(1% sample, 100 Adam steps, mini-batch 65,536, lr 1e-2); m = 1.25, eps = 3, tau = 1024.
+
+One step = the whole job on one resident input: sample + labels, training, prediction, partition,
+rounds, polish, merge/repair. Each timed step sorts its own copy of the input (1 GiB, larger than
+L2), so no L2 flush is needed. `value` is keys sorted per second over the whole job; the sort alone,
+the plain binary32 form, the roofline of the dominant kernel, an end-to-end figure through the
+host-array C entry point and the CPU oracle on a bounded sample are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_KEYS = 268_435_456
+ARCH = dict(layers=2, h1=64, h2=64)
+TRAIN = dict(translate="ordbits", sample_n=N_KEYS // 100, steps=100, batch=65536, lr=1e-2, seed=0)
+SORT = dict(m=1.25, eps=3, tau=1024)
+WORKLOAD = ("268,435,456 float32 keys lognormal(0,2) with 5% exact duplicates, keys only; "
+            "MLP 1-64-64-1 trained on the device (1% sample, 100 Adam steps, batch 65536, lr 1e-2); "
+            "m=1.25, eps=3, tau=1024")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]),
+                "sm_max_mhz": p.get("sm_max_mhz", 2070.0), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def oracle_job(n: int, seed: int = 2):
+    """The oracle as it stands: binary64 training on a 1% sample + sequential NN-sort."""
+    import workloads as W
+    from oracle import oracle as orc
+    keys = W.lognormal_dup_f32(n, seed=seed, sigma=2.0)
+    t0 = time.perf_counter()
+    model, _, _ = orc.train(keys, ARCH["layers"], ARCH["h1"], ARCH["h2"], orc.ORDBITS,
+                            sample_n=max(1, n // 100), steps=100, batch=0, lr=1e-2, seed=0)
+    out, _, _, _ = orc.nnsort_model(keys, model, SORT["m"], SORT["eps"], SORT["tau"])
+    dt = time.perf_counter() - t0
+    return n / dt / 1e6, dt
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return
+    n = 100_000
+    for _ in range(args.warmup):
+        oracle_job(n)
+    t = 0.0
+    for _ in range(args.steps):
+        _, dt = oracle_job(n)
+        t += dt
+    v = n * args.steps / t / 1e6
+    line = {"impl": "reference", "metric": "Mkeys/s", "value": v, "unit": "Mkeys/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample_keys": n},
+            "cpu_baseline": {"value": v, "unit": "Mkeys/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} keys of the same distribution per step, same model "
+                                       "and training recipe (1% sample, 100 full-batch steps)"},
+            "e2e": {"value": v, "unit": "Mkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_job(nns, keys, precision, stats=True):
+    model, hist = nns.train(keys, **ARCH, **TRAIN)
+    st = nns.sort(keys, None, model, precision=precision, stats=stats, **SORT)
+    return model, hist, st
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--n", type=int, default=N_KEYS)
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        return
+
+    import torch
+    import paper_1907_08817_gb300 as nns
+    import workloads as W
+    from paper_1907_08817_gb300 import _lib as L
+    torch.cuda.set_device(local)
+    n = args.n
+    if args.n != N_KEYS:
+        TRAIN["sample_n"] = max(1, n // 100)
+    pk = peaks()
+
+    host = W.lognormal_dup_f32(n, seed=2, sigma=2.0)
+    pristine = torch.from_numpy(host).cuda()
+    nbuf = args.steps + args.warmup
+    bufs = [pristine.clone() for _ in range(nbuf)]
+    torch.cuda.synchronize()
+
+    precision = args.precision
+    if precision == "auto":
+        precision = "bf16"
+        try:
+            probe = bufs[0][: 1 << 16].clone()
+            m0, _ = nns.train(probe, **ARCH, sample_n=1000, steps=1)
+            nns.sort(probe, None, m0, precision="bf16")
+        except nns.NNSortError as e:
+            if e.status != -7:
+                raise
+            precision = "fp32"
+
+    s = torch.cuda.current_stream()
+    # warm-up
+    for k in range(args.warmup):
+        run_job(nns, bufs[k], precision)
+    torch.cuda.synchronize()
+    # timed region: K whole jobs, each on its own resident input
+    launches0 = L.lib().nnsort_launch_count()
+    clk = Clocks(local)
+    with clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for k in range(args.steps):
+            run_job(nns, bufs[args.warmup + k], precision, stats=False)
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier(ws)
+    launches = L.lib().nnsort_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * n * args.steps / (ms_max / 1e3) / 1e6
+
+    # correctness of the timed outputs (cheap device check)
+    ref = torch.sort(pristine).values
+    ok = all(torch.equal(bufs[args.warmup + k].view(torch.int32), ref.view(torch.int32))
+             for k in range(args.steps))
+    assert ok, "sorted output differs from torch.sort"
+    del ref
+
+    # breakdown: training vs sort, per-stage timings (separate, untimed-for-value runs)
+    job = pristine.clone()
+    ta = torch.cuda.Event(enable_timing=True)
+    tb = torch.cuda.Event(enable_timing=True)
+    ta.record(s)
+    model, hist = nns.train(job, **ARCH, **TRAIN)
+    tb.record(s)
+    torch.cuda.synchronize()
+    train_ms = ta.elapsed_time(tb)
+    stage_runs = []
+    for _ in range(3):
+        job.copy_(pristine)
+        torch.cuda.synchronize()
+        st = nns.sort(job, None, model, precision=precision, timing=True, **SORT)
+        stage_runs.append(st["ms_stage"])
+    stage = [statistics.median(r[i] for r in stage_runs) for i in range(8)]
+    sort_ms = stage[7]
+
+    # the plain form: binary32 model, one launch sequence for this array
+    plain = None
+    if not args.no_plain and precision != "fp32":
+        pl = []
+        for _ in range(2):
+            job.copy_(pristine)
+            torch.cuda.synchronize()
+            st_p = nns.sort(job, None, model, precision="fp32", timing=True, **SORT)
+            pl.append(st_p["ms_stage"][7])
+        plain = {"precision": "fp32", "sort_ms": min(pl), "job_ms": train_ms + min(pl),
+                 "value": n / ((train_ms + min(pl)) / 1e3) / 1e6,
+                 "sort_only_mkeys_s": n / (min(pl) / 1e3) / 1e6,
+                 "sigma": st_p["sigma"], "trad_rate": st_p["trad_rate"]}
+
+    # roofline of the dominant kernel stage
+    kb = 4
+    names = ["predict", "partition", "bucket_bounds", "rounds", "finalize", "polish", "seam"]
+    dom = max(range(7), key=lambda i: stage[i])
+    npass = st["partition_passes"]
+    alg = {0: n * (kb + 4), 1: npass * n * 2 * (kb + 4), 2: 0, 3: n * (kb + 4 + 1), 4: 0,
+           5: n * (2 * kb + 5), 6: 0}
+    dom_ms = stage[dom]
+    if dom == 0 and precision == "bf16":
+        flops = n * 2 * 64 * 64
+        ach = flops / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": "predict (k_predict_bf16)", "bound": "tensor", "achieved": ach,
+                "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops"],
+                "traffic": None, "peak_source": pk["source"]}
+    elif dom == 0:
+        flops = n * 2 * (64 + 64 * 64 + 64)
+        fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        ach = flops / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": "predict (k_predict, binary32 FFMA)", "bound": "alu", "achieved": ach,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
+    else:
+        ach = alg[dom] / (dom_ms / 1e3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                "peak_source": pk["source"]}
+    # the whole sort against the path's algorithmic bytes (4 passes + 3 per re-mapped conflict)
+    w = st["w_size"]
+    b_alg = 4 * n * kb + 3 * sum(w[1:-1]) * kb if len(w) > 2 else 4 * n * kb
+    path = {"b_alg_bytes": b_alg, "sort_ms": sort_ms,
+            "frac_of_hbm": b_alg / (sort_ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+
+    # end to end through the host-array C entry point (pinned host buffers)
+    e2e = None
+    if rank == 0 or ws > 1:
+        hbuf = torch.from_numpy(host.copy()).pin_memory()
+        import ctypes as C
+        to = nns._topts(**ARCH, **TRAIN)
+        so = nns._sopts(SORT["m"], SORT["eps"], SORT["tau"], precision, 0, None, None, False)
+        tt = []
+        for k in range(max(2, min(args.steps, 3)) + 1):
+            hbuf.numpy()[:] = host
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc = L.lib().nnsort_train_sort_host(C.c_void_p(hbuf.data_ptr()), None, n, 0, C.byref(to),
+                                                C.byref(so), None, None, C.c_void_p(s.cuda_stream))
+            t1 = time.perf_counter()
+            L.check("nnsort_train_sort_host", rc)
+            if k:
+                tt.append(t1 - t0)
+        e2e = {"value": n / statistics.median(tt) / 1e6, "unit": "Mkeys/s",
+               "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        ncpu = 300_000
+        v, dt = oracle_job(ncpu)
+        cpu = {"value": v, "unit": "Mkeys/s", "cores": 1, "kind": "oracle",
+               "sample": f"{ncpu} keys of the same distribution, same model and recipe "
+                         f"(1% sample, 100 full-batch binary64 steps), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": "Mkeys/s", "value": value, "unit": "Mkeys/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if precision == "bf16" else "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "precision": precision,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (each timed step sorts its own 1 GiB copy)"},
+                "roofline": roof, "path": path,
+                "breakdown_ms": {"train": train_ms, "sort": sort_ms,
+                                 **{names[i]: stage[i] for i in range(7)}},
+                "sort_only_mkeys_s": n / (sort_ms / 1e3) / 1e6,
+                "stats": {"rounds": st["t"], "w_size": st["w_size"], "sigma": st["sigma"],
+                          "e": st["e"], "trad_rate": st["trad_rate"], "buckets": st["buckets"],
+                          "oversized_buckets": st["oversized_buckets"], "repaired": st["repaired"],
+                          "final_train_loss": float(hist[-1])},
+                "plain": plain, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -185,10 +185,11 @@ def predict(keys, model: Model, m: float = 1.25, precision="fp32", key_type=None
     return slots.to(torch.int64) & 0xFFFFFFFF, y
 
 
-def _sopts(m, eps, tau, precision, bucket_log2, slots, fate, no_sync) -> L.SortOpts:
+def _sopts(m, eps, tau, precision, bucket_log2, slots, fate, no_sync, timing=False) -> L.SortOpts:
     o = L.SortOpts()
     L.lib().nnsort_default_sort_opts(C.byref(o))
     o.m, o.eps, o.tau, o.precision, o.bucket_log2 = m, eps, tau, _prec(precision), bucket_log2
+    o.timing = 1 if timing else 0
     o.d_slots = None if slots is None else slots.data_ptr()
     o.d_fate = None if fate is None else fate.data_ptr()
     o.no_sync = 1 if no_sync else 0
@@ -197,14 +198,14 @@ def _sopts(m, eps, tau, precision, bucket_log2, slots, fate, no_sync) -> L.SortO
 
 def sort(keys, payload=None, model: Model | None = None, *, m=1.25, eps=3, tau=1024,
          precision="fp32", bucket_log2=0, slots=None, fate: bool = False, stats: bool = True,
-         key_type=None, stream=None):
+         timing: bool = False, key_type=None, stream=None):
     """NN-sort in place. `slots` (int32 device tensor of positions) replaces the model.
     Returns the stats dict (or None), plus the per-row fate tensor when fate=True."""
     torch = _torch()
     n = keys.numel()
     ft = torch.zeros(n, dtype=torch.int8, device=keys.device) if fate else None
-    o = _sopts(m, eps, tau, precision, bucket_log2, slots, ft, not stats)
-    st = L.Stats() if stats else None
+    o = _sopts(m, eps, tau, precision, bucket_log2, slots, ft, not stats, timing)
+    st = L.Stats() if (stats or timing) else None
     rc = L.lib().nnsort_sort(_ptr(keys), _ptr(payload), n, key_code(keys, key_type),
                              None if model is None else model.handle, C.byref(o),
                              None if st is None else C.byref(st), _stream(stream))
