@@ -228,6 +228,29 @@ int nnsort_sort_batch(void *const *d_keys, int32_t *const *d_payloads, const uin
                       int32_t count, int32_t dtype, const nnsort_model *const *fs,
                       const nnsort_sort_opts *o, nnsort_stats *st, cudaStream_t stream);
 
+/* ---- sorting without device allocation ------------------------------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that cannot allocate
+ * device memory when they sort: code whose memory budget was fixed up front, code that must not
+ * pay for (or synchronise on) cudaMalloc/cudaFree, and hosts whose allocator belongs to another
+ * framework. It runs the same method and kernels as nnsort_sort on one device array, but takes all
+ * of its scratch from one fixed device array that is part of the library image (about 13 MiB,
+ * held on every GPU that loads the library until the process exits). It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - n may be at most NNSORT_NOALLOC_MAX_N, and floor(n m) + 1 at most 1024 buckets of
+ *     2^bucket_log2 positions; larger requests return NNSORT_E_INVALID_ARG and touch nothing.
+ *   - f is required (o->d_slots and o->d_fate must be NULL).
+ *   - The first call on a device looks up the scratch's device address and clears its look-back
+ *     area (cudaGetSymbolAddress, cudaMemsetAsync); make that first call before any stream
+ *     capture.
+ *   - Every call shares the one scratch array and finds the previous call's contents there; each
+ *     call clears what must start at zero. Calls whose work overlaps on the GPU (for example on
+ *     two streams at once) race on the scratch and must be serialised by the caller.
+ *   - The call synchronises `stream` before returning and fills st (nullable) like nnsort_sort. */
+#define NNSORT_NOALLOC_MAX_N 262144
+int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtype,
+                        const nnsort_model *f, const nnsort_sort_opts *o, nnsort_stats *st,
+                        cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

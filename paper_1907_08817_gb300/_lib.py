@@ -112,6 +112,7 @@ def lib():
         "nnsort_sort_batch": (C.c_int, [P, P, P, i32, i32, P, P, P, P]),
         "nnsort_train_sort_host": (C.c_int, [P, P, u64, i32, P, P, P, P, P]),
         "nnsort_launch_count": (u64, []),
+        "nnsort_sort_noalloc": (C.c_int, [P, P, u64, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -135,4 +136,4 @@ def exported_symbols() -> list[str]:
             "nnsort_model_save", "nnsort_model_load", "nnsort_sample_labels", "nnsort_train",
             "nnsort_mlp_forward", "nnsort_mlp_backward", "nnsort_mlp_loss_grad",
             "nnsort_predict", "nnsort_sort", "nnsort_sort_host", "nnsort_sort_batch",
-            "nnsort_train_sort_host", "nnsort_launch_count"]
+            "nnsort_train_sort_host", "nnsort_launch_count", "nnsort_sort_noalloc"]
