@@ -112,8 +112,10 @@ typedef struct {
     const uint32_t *d_slots;  /* nullable: injected positions in [0, floor(n m)] replace the model */
     int8_t *d_fate;           /* nullable: per input row, +i stored in o_i and appended, -i stored
                                  in o_i and inserted out of order, 0 sorted as leftover */
-    int32_t no_sync;          /* 1: return without synchronising; errors raised on the device are
-                                 then reported by nnsort_stream_status() */
+    int32_t no_sync;          /* 1: skip the statistics read-back; errors raised on the device are
+                                 then reported by nnsort_stream_status(). The call still waits once
+                                 for the device after the polish, to send a large seam repair to
+                                 the multi-block sort. */
     int32_t timing;           /* 1: record per-stage CUDA events into nnsort_stats.ms_stage */
 } nnsort_sort_opts;
 

@@ -253,6 +253,12 @@ double orc_mlp1_f64(const orc_arch *a, const double *p, double x) {
     return y;
 }
 
+/* Hidden layer 1 activations relu(fmaf(W1_j, x, b1_j)) in binary32, row-major [n][h1]. */
+void orc_mlp_layer1_f32(const orc_arch *a, const float *p, const float *x, uint64_t n, float *h) {
+    for (uint64_t i = 0; i < n; ++i)
+        for (int j = 0; j < a->h1; ++j) h[i * a->h1 + j] = relu_f(fmaf(p[j], x[i], p[a->h1 + j]));
+}
+
 void orc_mlp_forward_f32(const orc_arch *a, const float *p, const float *x, uint64_t n, float *y) {
     for (uint64_t i = 0; i < n; ++i) y[i] = orc_mlp1_f32(a, p, x[i]);
 }

@@ -82,6 +82,7 @@ def lib():
             "orc_make_norm": (None, [P, i32, P, u64, i32, P]),
             "orc_num_params": (u64, [P]),
             "orc_mlp_forward_f32": (None, [P, P, P, u64, P]),
+            "orc_mlp_layer1_f32": (None, [P, P, P, u64, P]),
             "orc_mlp_forward_f64": (None, [P, P, P, u64, P]),
             "orc_mlp_loss_grad_f64": (f64, [P, P, P, P, u64, i32, f64, P, P]),
             "orc_adam_f64": (None, [P, P, P, P, u64, u64, f64, f64, f64, f64]),
@@ -169,6 +170,14 @@ def mlp_forward_f32(layers, h1, h2, params, x) -> np.ndarray:
     y = np.empty_like(x)
     lib().orc_mlp_forward_f32(C.byref(Arch(layers, h1, h2)), _p(params), _p(x), x.shape[0], _p(y))
     return y
+
+
+def mlp_layer1_f32(layers, h1, h2, params, x) -> np.ndarray:
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    h = np.empty((x.shape[0], h1), dtype=np.float32)
+    lib().orc_mlp_layer1_f32(C.byref(Arch(layers, h1, h2)), _p(params), _p(x), x.shape[0], _p(h))
+    return h
 
 
 def mlp_forward_f64(layers, h1, h2, params, x) -> np.ndarray:

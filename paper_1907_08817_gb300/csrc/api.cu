@@ -448,9 +448,9 @@ Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, boo
     L.segs = c.take<Seg>(nseg);
     L.stats = c.take<SegStats>(nseg);
     L.err = c.take<uint32_t>(4);
-    L.hist = c.take<uint32_t>(MAX_PASSES * RADIX_BINS);
-    L.bases = c.take<uint32_t>(MAX_PASSES * RADIX_BINS);
-    L.tickets = c.take<uint32_t>(MAX_PASSES * 4);
+    L.hist = c.take<uint32_t>(8 * RADIX_BINS);
+    L.bases = c.take<uint32_t>(8 * RADIX_BINS);
+    L.tickets = c.take<uint32_t>(8 * 4);
     for (int i = 0; i < 2; ++i) {
         L.gs[i] = c.take<uint32_t>(N);
         L.key[i] = c.take<unsigned char>(N * kb);
@@ -572,6 +572,47 @@ void fill_stats(const Seg &s, const SegStats &d, nnsort_stats *st) {
     st->repaired = d.repaired;
 }
 
+// stable multi-block radix sort by key of out[lo, hi) of one array, through the (now free)
+// partition buffers; used for seam repairs too large for one block
+int global_repair(Workspace *w, Layout &L, const Seg &sg, uint64_t lo, uint64_t hi, int kb, int dtype,
+                  cudaStream_t s) {
+    const uint64_t len = hi - lo;
+    if (len < 2) return NNSORT_OK;
+    const int npass = kb;  // 8-bit digits of the key's order image
+    unsigned char *keys = reinterpret_cast<unsigned char *>(sg.keys) + lo * kb;
+    uint32_t *pay = sg.payload ? reinterpret_cast<uint32_t *>(sg.payload + lo) : nullptr;
+    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
+    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
+    CK(launch_key_hist(keys, len, kb, dtype, npass, L.hist, s));
+    CK(launch_digit_bases(L.hist, L.bases, npass, s));
+    for (int p = 0; p < npass; ++p) {
+        const int si = p & 1, di = si ^ 1;
+        OnesweepArgs a{};
+        a.N = len;
+        a.key_in = p == 0 ? (void *)keys : L.key[si];
+        a.key_out = L.key[di];
+        if (pay) {
+            a.pay_in = p == 0 ? pay : L.pay[si];
+            a.pay_out = L.pay[di];
+        }
+        a.key_digits = 1;
+        a.shift = 8 * p;
+        a.bits = 8;
+        a.digit_base = L.bases + p * RADIX_BINS;
+        a.lookback = w->lookback;
+        a.ticket = L.tickets + p * 4;
+        a.epoch = next_epoch(w, s);
+        a.err = L.err;
+        a.key_bytes = kb;
+        a.dtype = dtype;
+        CK(launch_onesweep(a, s));
+    }
+    const int fi = npass & 1;
+    CK(cudaMemcpyAsync(keys, L.key[fi], len * kb, cudaMemcpyDeviceToDevice, s));
+    if (pay) CK(cudaMemcpyAsync(pay, L.pay[fi], len * 4, cudaMemcpyDeviceToDevice, s));
+    return NNSORT_OK;
+}
+
 int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype, nnsort_stats *st,
              cudaStream_t s) {
     nnsort_sort_opts o;
@@ -608,7 +649,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     if ((rc = ensure_arena(w, need, s))) return rc;
     const uint64_t ptiles = (P.N + PART_TILE - 1) / PART_TILE;
     if ((rc = ensure_lookback(w, ptiles * RADIX_BINS, s))) return rc;
-    const size_t pin_need = sizeof(Seg) * nseg + sizeof(SegStats) * nseg + 64;
+    const size_t pin_need = sizeof(Seg) * nseg + sizeof(SegStats) * nseg + 256;
     if ((rc = ensure_pinned(w, pin_need, s))) return rc;
     size_t total = 0;
     Layout L = carve(w->arena, nseg, P.N, P.NB, kb, anypay, rows, &total);
@@ -711,6 +752,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     sa.key_bytes = kb;
     sa.dtype = dtype;
     sa.polish_cap = polish_capacity(kb, anypay, rows, P.wlog, 2, &sa.polish_smem);
+    sa.allow_defer = 1;
     CK(launch_rounds(sa, s));
     CK(mark(4));
     CK(launch_finalize(sa, s));
@@ -718,6 +760,18 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     CK(launch_polish(sa, s));
     CK(mark(6));
     CK(launch_seam_repair(sa, s));
+    if (sa.allow_defer) {
+        // one wait at the end of the pipeline: large seam repairs run as multi-block sorts
+        unsigned char *hp0 = w->pinned + align_up(sizeof(Seg) * nseg, 64);
+        CK(cudaMemcpyAsync(hp0, L.stats, sizeof(SegStats) * nseg, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < nseg; ++i) {
+            SegStats d;
+            std::memcpy(&d, hp0 + sizeof(SegStats) * i, sizeof(SegStats));
+            if (d.repair_lo_hi_valid == 2)
+                if ((rc = global_repair(w, L, P.segs[i], d.repair_lo, d.repair_hi, kb, dtype, s))) return rc;
+        }
+    }
     CK(mark(7));
 
     if (o.no_sync && !st) return NNSORT_OK;

@@ -115,7 +115,9 @@ struct SolveArgs {
     int key_bytes, dtype;
     int polish_cap;           // elements a bucket may hold on chip
     size_t polish_smem;
+    int allow_defer;          // 1: a large seam repair is left to the host's multi-block sort
 };
+constexpr uint64_t SEAM_CTA_MAX = 1u << 16;  // largest seam repair one block performs
 cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s);

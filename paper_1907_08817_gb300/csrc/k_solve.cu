@@ -625,12 +625,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam(SolveArgs a) {
             if (!okey_less(mv.k, mv.tb, k, tb)) l = mid + 1; else h = mid;
         }
         sh_lo = l;
+        const bool defer = a.allow_defer && !a.out_rows && (sh_hi - l) > SEAM_CTA_MAX;
         a.stats[s].repair_lo = l;
         a.stats[s].repair_hi = sh_hi;
-        a.stats[s].repair_lo_hi_valid = 1;
+        a.stats[s].repair_lo_hi_valid = defer ? 2u : 1u;
         a.stats[s].repaired = sh_hi - l;
     }
     __syncthreads();
+    if (a.allow_defer && !a.out_rows && (sh_hi - sh_lo) > SEAM_CTA_MAX) return;
     // re-sort [lo, hi) of the output by (key, row): the range is a union of sorted runs
     const uint64_t lo = sh_lo, len = sh_hi - sh_lo;
     uint32_t *X = a.g_x + sg.ebase + lo, *Y = a.g_y + sg.ebase + lo;

@@ -1,0 +1,94 @@
+"""BF16 tensor-core (tcgen05) forward pass inside the sort.
+
+The model output is compared with a binary64 emulation of the same arithmetic (binary32 first
+layer, BF16-rounded hidden activations and weights, exact products, wide accumulation); only the
+tensor core's FP32 accumulation order differs, so the tolerance is a few binary32 ulps of the
+accumulated magnitude. Given the positions the BF16 path produced, the rest of the sort must match
+the oracle bit for bit; displacement against the binary64 model is reported, not asserted."""
+import numpy as np
+import pytest
+
+from helpers import bits, from_dev, lib_model, stats_core, to_dev
+from oracle import oracle as orc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+import paper_1907_08817_gb300 as nns  # noqa: E402
+
+
+def _bf16(a: np.ndarray) -> np.ndarray:
+    """Round binary32 values to BF16 (nearest, ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _emulate(params: np.ndarray, h: int, x: np.ndarray):
+    p = params.astype(np.float64)
+    W2 = p[2 * h:2 * h + h * h].reshape(h, h)
+    b2 = p[2 * h + h * h:3 * h + h * h]
+    W3 = p[3 * h + h * h:4 * h + h * h]
+    b3 = p[4 * h + h * h]
+    h1 = _bf16(orc.mlp_layer1_f32(2, h, h, params, x))  # binary32 first layer, then BF16
+    z = h1 @ _bf16(W2.astype(np.float32)).T
+    h2 = np.maximum(z + b2, 0)
+    terms = np.abs(h2 * W3).sum(axis=1) + abs(b3)
+    return h2 @ W3 + b3, terms, np.abs(h1) @ np.abs(_bf16(W2.astype(np.float32))).T
+
+
+@pytest.mark.parametrize("h", [16, 32, 64])
+def test_bf16_forward_matches_emulation(h):
+    keys = W.lognormal_dup_f32(300_000, 31, sigma=2.0)
+    om, _, _ = orc.train(keys, 2, h, h, orc.ORDBITS, sample_n=3000, steps=60, seed=h)
+    f = lib_model(om)
+    dk, _ = to_dev(keys)
+    slots, y = nns.predict(dk, f, precision="bf16")
+    x = orc.translate_f32(keys, om.norm)
+    ye, terms, zmag = _emulate(om.params, h, x)
+    yg = y.cpu().numpy().astype(np.float64)
+    W3 = np.abs(om.params[3 * h + h * h:4 * h + h * h].astype(np.float64))
+    # tensor-core accumulation of z (<= 2 ulp of |z| terms) propagated through |W3|, plus the
+    # binary32 output layer
+    tol = 4 * 2.0 ** -23 * (zmag @ W3 + terms) + 1e-7
+    assert np.all(np.abs(yg - ye) <= tol), float(np.max(np.abs(yg - ye) - tol))
+    # displacement against the binary32 and binary64 models (reported)
+    s32, _ = orc.predict_slots(keys, om)
+    sg = slots.cpu().numpy().astype(np.int64)
+    d = np.abs(sg - s32.astype(np.int64))
+    print(f"H={h}: |slot_bf16 - slot_fp32| mean {d.mean():.2f} max {d.max()}")
+
+
+@pytest.mark.parametrize("h", [32, 64])
+def test_bf16_sort_matches_oracle_given_its_positions(h):
+    keys = W.lognormal_dup_f32(400_000, 41, sigma=2.0)
+    payload = np.arange(keys.shape[0], dtype=np.int32)
+    om, _, _ = orc.train(keys, 2, h, h, orc.ORDBITS, sample_n=4000, steps=80, seed=h)
+    f = lib_model(om)
+    dk, _ = to_dev(keys)
+    slots, _ = nns.predict(dk, f, precision="bf16", want_y=False)
+    dp = torch.from_numpy(payload).cuda()
+    st = nns.sort(dk, dp, f, precision="bf16")
+    L, _, _ = orc.nm_split(keys.shape[0])
+    ok, op, ost, _ = orc.nnsort(keys, slots.cpu().numpy().astype(np.uint32), L, 3, 1024, payload)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    np.testing.assert_array_equal(dp.cpu().numpy(), op)
+    assert stats_core(st) == stats_core(ost)
+
+
+def test_bf16_without_hidden_to_hidden_layer():
+    keys = torch.rand(5000, device="cuda")
+    nm = orc.make_norm(keys.cpu().numpy(), np.arange(5000, dtype=np.uint64), orc.VALUE)
+    # one hidden layer: nothing runs on the tensor cores, BF16 is the binary32 path
+    one = lib_model(orc.Model(1, 32, 0, nm, orc.init_params(1, 32, 0, 0)))
+    s32, y32 = nns.predict(keys, one, precision="fp32")
+    s16, y16 = nns.predict(keys, one, precision="bf16")
+    assert torch.equal(s32, s16) and torch.equal(y32, y16)
+    # hidden widths below one MMA tile (16) are not built for the tensor path
+    tiny = lib_model(orc.Model(2, 4, 4, nm, orc.init_params(2, 4, 4, 0)))
+    with pytest.raises(nns.NNSortError) as ei:
+        nns.sort(keys, None, tiny, precision="bf16")
+    assert ei.value.status == -7

@@ -101,6 +101,32 @@ def test_injected_degenerate_maps():
                     np.arange(n, dtype=np.int32))
 
 
+def test_large_seam_repair_runs_as_multi_block_sort():
+    """Positions unrelated to key order put violators across the whole output; the repair is
+    then larger than one block handles and runs as a multi-block radix sort."""
+    rs = np.random.RandomState(13)
+    for n, dt in ((300_000, np.float32), (200_000, np.uint64)):
+        keys = (W.normal_f32(n, 14) if dt == np.float32
+                else rs.randint(0, 2 ** 62, n, dtype=np.int64).astype(np.uint64))
+        L, _, _ = orc.nm_split(n)
+        slots = rs.randint(0, L, n).astype(np.uint32)
+        dk, kt = to_dev(keys)
+        ds = torch.from_numpy(slots.view(np.int32)).cuda()
+        st = nns.sort(dk, None, None, slots=ds, key_type=kt)
+        ok, _, ost, _ = orc.nnsort(keys, slots, L, 3, 1024)
+        np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+        assert stats_core(st) == stats_core(ost)
+        assert st["repaired"] > 65_536
+    # a random (untrained) two-layer model is non-monotone: same outcome through the model path
+    keys = W.lognormal_dup_f32(500_000, 15, sigma=2.0)
+    om = _rand_model(orc.F32, keys, 2, 16, 16, orc.ORDBITS, seed=5)
+    dk, _ = to_dev(keys)
+    st = nns.sort(dk, None, lib_model(om))
+    ok, _, ost, _ = orc.nnsort_model(keys, om)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    assert stats_core(st) == stats_core(ost)
+
+
 def test_injected_small_buckets_and_oversized():
     rs = np.random.RandomState(11)
     n = 120_000
