@@ -68,17 +68,24 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_onesweep(OnesweepArgs a) {
     uint16_t wr[PART_ITEMS];
     const W *kin = reinterpret_cast<const W *>(a.key_in);
     const unsigned lt = (1u << lane) - 1u;
+    // all of the tile's loads first, so they are in flight together
 #pragma unroll
     for (int r = 0; r < PART_ITEMS; ++r) {
         const uint32_t loc = (uint32_t)w * (32 * PART_ITEMS) + r * 32 + lane;
-        const bool valid = loc < cnt_tile;
         const uint64_t e = base + loc;
-        uint32_t d = 0xFFFFu;
-        if (valid) {
+        if (loc < cnt_tile) {
             key[r] = kin[e];
             if constexpr (!KEYDIG) gsv[r] = a.gs_in[e];
             if constexpr (PAY) pay[r] = a.pay_in[e];
             if constexpr (ROW) row[r] = a.row_in[e];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PART_ITEMS; ++r) {
+        const uint32_t loc = (uint32_t)w * (32 * PART_ITEMS) + r * 32 + lane;
+        const bool valid = loc < cnt_tile;
+        uint32_t d = 0xFFFFu;
+        if (valid) {
             if constexpr (KEYDIG)
                 d = (uint32_t)(ordbits(word64(key[r]), a.dtype) >> a.shift) & mask;
             else

@@ -323,6 +323,7 @@ struct PolishSmem {
     uint32_t scratch[33];
     KMax kscratch[33];
     uint32_t rl_off[MAXR + 1];
+    KMax carry[MAXR];
     unsigned int ooo[MAXR];
     int seg, t;
 };
@@ -360,6 +361,12 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
     for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.F[i] = (v.R[i] >= t) ? 1 : 0;
     if (tid <= MAXR) sm.rl_off[tid] = 0;
     if (tid < MAXR) sm.ooo[tid] = 0;
+    if (tid < t) {
+        const OKey cr = a.carry[(size_t)b * MAXR + tid];
+        sm.carry[tid].k = cr.k;
+        sm.carry[tid].tb = cr.tb;
+        sm.carry[tid].valid = cr.valid;
+    }
     __syncthreads();
     uint32_t rl_n = 0;
     for (int r = 0; r < t; ++r) {
@@ -389,9 +396,7 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
         }
         KMax run = block_excl_max(loc, sm.kscratch, nullptr);
         {
-            const OKey cr = a.carry[(size_t)b * MAXR + r];
-            KMax cc; cc.k = cr.k; cc.tb = cr.tb; cc.valid = cr.valid;
-            run = kmax(cc, run);
+            run = kmax(sm.carry[r], run);
         }
         uint32_t kept = 0, evicted = 0;
         for (uint32_t q = q0; q < q1; ++q) {
@@ -516,12 +521,35 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
         uint8_t *R = p; p += cap;
         uint8_t *F = p; p += cap;
         const W *gk = reinterpret_cast<const W *>(a.keys) + s0;
-        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) {
-            K[i] = gk[i];
-            S16[i] = (uint16_t)(a.gs[s0 + i] & (Wn - 1u));
-            R[i] = a.rank[s0 + i];
-            if (P) P[i] = a.pay[s0 + i];
-            if (T) T[i] = a.rows[s0 + i];
+        const uint32_t *gg = a.gs + s0;
+        const uint8_t *gr = a.rank + s0;
+        constexpr int LB = 8;  // items per thread whose loads are issued together
+        for (uint32_t b0 = 0; b0 < nbk; b0 += SOLVE_THREADS * LB) {
+            W kr[LB];
+            uint32_t sr[LB], pr[LB], tr[LB];
+            uint8_t rr[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = b0 + q * SOLVE_THREADS + tid;
+                if (i < nbk) {
+                    kr[q] = gk[i];
+                    sr[q] = gg[i];
+                    rr[q] = gr[i];
+                    if (P) pr[q] = a.pay[s0 + i];
+                    if (T) tr[q] = a.rows[s0 + i];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = b0 + q * SOLVE_THREADS + tid;
+                if (i < nbk) {
+                    K[i] = kr[q];
+                    S16[i] = (uint16_t)(sr[q] & (Wn - 1u));
+                    R[i] = rr[q];
+                    if (P) P[i] = pr[q];
+                    if (T) T[i] = tr[q];
+                }
+            }
         }
         __syncthreads();
         BucketView<W, uint16_t> v{K, S16, nullptr, R, F, P, T, X, Y, RL,

@@ -254,6 +254,213 @@ __global__ void __launch_bounds__(TR_THREADS) k_grad(GradArgs g) {
     if (tid == 0 && g.loss_partials) g.loss_partials[blockIdx.x] = lacc;
 }
 
+// Two hidden layers of width H (32 or 64): the per-chunk work as three register-tiled block
+// products over all threads (C = 64 samples per chunk, 4x4 outputs per thread):
+//   Z  = b2 + H1 W2^T        (forward, accumulated over j in the oracle's order)
+//   D1 = [H1 > 0] (D2 W2)    (backward), D2 = [Z > 0] gy W3
+//   dW2 += D2^T H1           (kept in registers across the block's chunks)
+// Every sum runs in a fixed order, so the gradient is reproducible.
+constexpr int GC = 64;          // samples per chunk
+template <int H> struct GemmSmem {
+    static constexpr int LD = H + 4;  // row stride: 16-byte rows, no bank conflicts
+    static constexpr int P = 2 * H + H * H + 2 * H + 1;
+    static constexpr int OFF_W2T = (P + 3) & ~3;
+    static constexpr int OFF_H1 = OFF_W2T + H * LD;
+    static constexpr int OFF_H2 = OFF_H1 + GC * LD;
+    static constexpr int OFF_D2 = OFF_H2 + GC * LD;
+    static constexpr int OFF_D1 = OFF_D2 + GC * LD;
+    static constexpr int OFF_X = OFF_D1 + GC * LD;
+    static constexpr int OFF_GY = OFF_X + GC;
+    static constexpr int OFF_L = OFF_GY + GC;
+    static constexpr int FLOATS = OFF_L + GC;
+};
+
+template <int H>
+__global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
+    using S = GemmSmem<H>;
+    constexpr int LD = S::LD, P = S::P;
+    constexpr int TN = H / 16;  // outputs per thread along the width (4 for H = 64, 2 for H = 32)
+    static_assert(H == 32 || H == 64, "block-product gradient widths");
+    extern __shared__ __align__(16) float sm[];
+    float *sp = sm, *W2T = sm + S::OFF_W2T, *sH1 = sm + S::OFF_H1, *sH2 = sm + S::OFF_H2;
+    float *sD2 = sm + S::OFF_D2, *sD1 = sm + S::OFF_D1, *sX = sm + S::OFF_X, *sGY = sm + S::OFF_GY;
+    float *sL = sm + S::OFF_L;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < P; i += TR_THREADS) sp[i] = g.params[i];
+    __syncthreads();
+    const float *W1 = sp, *b1 = sp + H, *W2 = sp + 2 * H, *b2 = W2 + H * H, *W3 = b2 + H;
+    const float b3 = W3[H];
+    for (int e = tid; e < H * H; e += TR_THREADS) {  // W2T[j][k] = W2[k][j]
+        const int k = e / H, j = e % H;
+        W2T[j * LD + k] = W2[e];
+    }
+    // thread tiles: rows m0..m0+3 (samples), columns n0..n0+TN-1
+    const int tm = tid / 16, tn = tid % 16;
+    const int m0 = 4 * tm, n0 = TN * tn;
+    // dW2 tile: rows k0..k0+TK-1, columns j0..j0+TN-1 over the H x H gradient
+    constexpr int TK = (H * H) / (TR_THREADS * TN);  // 4 for H = 64, 2 for H = 32
+    const int k0 = TK * tm, j0 = TN * tn;
+    float aW2[TK][TN];
+#pragma unroll
+    for (int i = 0; i < TK; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) aW2[i][q] = 0.0f;
+    float aV = 0.0f, aV2 = 0.0f;  // per-thread vector gradients (see the role split below)
+    float lacc = 0.0f;
+    const uint64_t per = (g.n + gridDim.x - 1) / gridDim.x;
+    const uint64_t i0 = std::min<uint64_t>(g.n, (uint64_t)blockIdx.x * per);
+    const uint64_t i1 = std::min<uint64_t>(g.n, i0 + per);
+    __syncthreads();
+    for (uint64_t c0 = i0; c0 < i1; c0 += GC) {
+        const int cn = (int)std::min<uint64_t>(GC, i1 - c0);
+        uint64_t src = 0;
+        if (tid < GC) {
+            float x = 0.0f;
+            if (tid < cn) {
+                src = c0 + tid;
+                if (g.mode == 2) src = __umul64hi(rng_draw(g.bseed, g.bofs + c0 + tid), g.S);
+                x = g.x[src];
+            }
+            sX[tid] = x;
+        }
+        __syncthreads();
+        for (int e = tid; e < GC * H; e += TR_THREADS) {
+            const int s = e / H, j = e % H;
+            sH1[s * LD + j] = (s < cn) ? relu_f(__fmaf_rn(W1[j], sX[s], b1[j])) : 0.0f;
+        }
+        __syncthreads();
+        {   // Z = b2 + H1 W2^T, then H2 = relu(Z)
+            float acc[4][TN];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < TN; ++q) acc[i][q] = b2[n0 + q];
+#pragma unroll 8
+            for (int j = 0; j < H; ++j) {
+                float a[4], b[TN];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = sH1[(m0 + i) * LD + j];
+#pragma unroll
+                for (int q = 0; q < TN; ++q) b[q] = W2T[j * LD + n0 + q];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int q = 0; q < TN; ++q) acc[i][q] = __fmaf_rn(b[q], a[i], acc[i][q]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < TN; ++q) sH2[(m0 + i) * LD + n0 + q] = relu_f(acc[i][q]);
+        }
+        __syncthreads();
+        if (tid < GC) {  // output, loss, upstream gradient per sample
+            float gy = 0.0f, lv = 0.0f;
+            if (tid < cn) {
+                float y = b3;
+                for (int k = 0; k < H; ++k) y = __fmaf_rn(W3[k], sH2[tid * LD + k], y);
+                if (g.mode == 0) {
+                    gy = g.gy[c0 + tid];
+                } else {
+                    const float r = y - g.label[src];
+                    if (g.loss == NNSORT_LOSS_HUBER) {
+                        const float ar = fabsf(r);
+                        lv = (ar <= g.delta) ? 0.5f * r * r : g.delta * ar - 0.5f * g.delta * g.delta;
+                        gy = (r > g.delta) ? g.delta : ((r < -g.delta) ? -g.delta : r);
+                    } else {
+                        lv = r * r;
+                        gy = 2.0f * r;
+                    }
+                    gy *= g.inv_n;
+                }
+            }
+            sGY[tid] = gy;
+            sL[tid] = lv;
+        }
+        __syncthreads();
+        for (int e = tid; e < GC * H; e += TR_THREADS) {
+            const int s = e / H, k = e % H;
+            sD2[s * LD + k] = (sH2[s * LD + k] > 0.0f) ? sGY[s] * W3[k] : 0.0f;
+        }
+        __syncthreads();
+        {   // D1 = [H1 > 0] (D2 W2)
+            float acc[4][TN];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < TN; ++q) acc[i][q] = 0.0f;
+#pragma unroll 8
+            for (int k = 0; k < H; ++k) {
+                float a[4], b[TN];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = sD2[(m0 + i) * LD + k];
+#pragma unroll
+                for (int q = 0; q < TN; ++q) b[q] = W2[k * H + n0 + q];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int q = 0; q < TN; ++q) acc[i][q] = __fmaf_rn(a[i], b[q], acc[i][q]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < TN; ++q)
+                    sD1[(m0 + i) * LD + n0 + q] = (sH1[(m0 + i) * LD + n0 + q] > 0.0f) ? acc[i][q] : 0.0f;
+        }
+        __syncthreads();
+        if (g.gx && tid < cn) {
+            float gx = 0.0f;
+            for (int j = 0; j < H; ++j) gx = __fmaf_rn(sD1[tid * LD + j], W1[j], gx);
+            g.gx[c0 + tid] = gx;
+        }
+        // dW2 += D2^T H1 over this chunk's samples
+#pragma unroll 4
+        for (int s = 0; s < cn; ++s) {
+            float a[TK], b[TN];
+#pragma unroll
+            for (int i = 0; i < TK; ++i) a[i] = sD2[s * LD + k0 + i];
+#pragma unroll
+            for (int q = 0; q < TN; ++q) b[q] = sH1[s * LD + j0 + q];
+#pragma unroll
+            for (int i = 0; i < TK; ++i)
+#pragma unroll
+                for (int q = 0; q < TN; ++q) aW2[i][q] = __fmaf_rn(a[i], b[q], aW2[i][q]);
+        }
+        // vectors: t < H -> (db2_t, dW3_t); H <= t < 2H -> (db1_j, dW1_j); t == 2H -> db3
+        if (tid < H) {
+            for (int s = 0; s < cn; ++s) {
+                aV = __fadd_rn(aV, sD2[s * LD + tid]);
+                aV2 = __fmaf_rn(sGY[s], sH2[s * LD + tid], aV2);
+            }
+        } else if (tid < 2 * H) {
+            const int j = tid - H;
+            for (int s = 0; s < cn; ++s) {
+                aV = __fadd_rn(aV, sD1[s * LD + j]);
+                aV2 = __fmaf_rn(sD1[s * LD + j], sX[s], aV2);
+            }
+        } else if (tid == 2 * H) {
+            for (int s = 0; s < cn; ++s) aV = __fadd_rn(aV, sGY[s]);
+        }
+        if (tid == TR_THREADS - 1)
+            for (int s = 0; s < cn; ++s) lacc = __fadd_rn(lacc, sL[s]);
+        __syncthreads();
+    }
+    float *out = g.partials + (size_t)blockIdx.x * P;
+#pragma unroll
+    for (int i = 0; i < TK; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) out[2 * H + (k0 + i) * H + j0 + q] = aW2[i][q];
+    if (tid < H) {
+        out[2 * H + H * H + tid] = aV;       // b2
+        out[3 * H + H * H + tid] = aV2;      // W3
+    } else if (tid < 2 * H) {
+        out[H + (tid - H)] = aV;             // b1
+        out[tid - H] = aV2;                  // W1
+    } else if (tid == 2 * H) {
+        out[P - 1] = aV;                     // b3
+    }
+    if (tid == TR_THREADS - 1 && g.loss_partials) g.loss_partials[blockIdx.x] = lacc;
+}
+
 template <int H1, int H2> static size_t grad_smem() {
     constexpr int P = (H2 == 0) ? (3 * H1 + 1) : (2 * H1 + H2 * H1 + 2 * H2 + 1);
     constexpr int H2e = H2 ? H2 : 1;
@@ -275,6 +482,15 @@ static cudaError_t grad_go(const GradArgs &g, int blocks, cudaStream_t s) {
     return nns_launched(cudaGetLastError());
 }
 
+template <int H>
+static cudaError_t grad_gemm_go(const GradArgs &g, int blocks, cudaStream_t s) {
+    const size_t smem = sizeof(float) * GemmSmem<H>::FLOATS;
+    cudaError_t e = cudaFuncSetAttribute(k_grad_gemm<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_grad_gemm<H><<<blocks, TR_THREADS, smem, s>>>(g);
+    return nns_launched(cudaGetLastError());
+}
+
 static cudaError_t grad_dispatch(const PadArch &a, const GradArgs &g, int blocks, cudaStream_t s) {
     if (a.layers == 1) {
         switch (a.h1) {
@@ -287,8 +503,8 @@ static cudaError_t grad_dispatch(const PadArch &a, const GradArgs &g, int blocks
         switch (a.h1) {
         case 8: return grad_go<8, 8>(g, blocks, s);
         case 16: return grad_go<16, 16>(g, blocks, s);
-        case 32: return grad_go<32, 32>(g, blocks, s);
-        case 64: return grad_go<64, 64>(g, blocks, s);
+        case 32: return grad_gemm_go<32>(g, blocks, s);
+        case 64: return grad_gemm_go<64>(g, blocks, s);
         }
     }
     return cudaErrorInvalidValue;
