@@ -117,6 +117,9 @@ typedef struct {
                                  for the device after the polish, to send a large seam repair to
                                  the multi-block sort. */
     int32_t timing;           /* 1: record per-stage CUDA events into nnsort_stats.ms_stage */
+    int32_t polish_blocks;    /* 0: automatic (3); 1, 2 or 3 polish blocks per SM: fewer blocks
+                                 let a bucket hold more keys on chip, more blocks leave more L1
+                                 and overlap more buckets */
 } nnsort_sort_opts;
 
 /* Per-array statistics (Sec. "Model Analysis", Eq. (sorting rate), Eq. (ratio)). */

@@ -185,11 +185,13 @@ def predict(keys, model: Model, m: float = 1.25, precision="fp32", key_type=None
     return slots.to(torch.int64) & 0xFFFFFFFF, y
 
 
-def _sopts(m, eps, tau, precision, bucket_log2, slots, fate, no_sync, timing=False) -> L.SortOpts:
+def _sopts(m, eps, tau, precision, bucket_log2, slots, fate, no_sync, timing=False,
+           polish_blocks=0) -> L.SortOpts:
     o = L.SortOpts()
     L.lib().nnsort_default_sort_opts(C.byref(o))
     o.m, o.eps, o.tau, o.precision, o.bucket_log2 = m, eps, tau, _prec(precision), bucket_log2
     o.timing = 1 if timing else 0
+    o.polish_blocks = polish_blocks
     o.d_slots = None if slots is None else slots.data_ptr()
     o.d_fate = None if fate is None else fate.data_ptr()
     o.no_sync = 1 if no_sync else 0
@@ -198,13 +200,13 @@ def _sopts(m, eps, tau, precision, bucket_log2, slots, fate, no_sync, timing=Fal
 
 def sort(keys, payload=None, model: Model | None = None, *, m=1.25, eps=3, tau=1024,
          precision="fp32", bucket_log2=0, slots=None, fate: bool = False, stats: bool = True,
-         timing: bool = False, key_type=None, stream=None):
+         timing: bool = False, polish_blocks: int = 0, key_type=None, stream=None):
     """NN-sort in place. `slots` (int32 device tensor of positions) replaces the model.
     Returns the stats dict (or None), plus the per-row fate tensor when fate=True."""
     torch = _torch()
     n = keys.numel()
     ft = torch.zeros(n, dtype=torch.int8, device=keys.device) if fate else None
-    o = _sopts(m, eps, tau, precision, bucket_log2, slots, ft, not stats, timing)
+    o = _sopts(m, eps, tau, precision, bucket_log2, slots, ft, not stats, timing, polish_blocks)
     st = L.Stats() if (stats or timing) else None
     rc = L.lib().nnsort_sort(_ptr(keys), _ptr(payload), n, key_code(keys, key_type),
                              None if model is None else model.handle, C.byref(o),
@@ -233,7 +235,7 @@ def sort_host(keys: np.ndarray, payload: np.ndarray | None = None, model: Model 
 
 
 def sort_batch(keys_list, models, payloads=None, *, m=1.25, eps=3, tau=1024, precision="fp32",
-               bucket_log2=0, stats=True, key_type=None, stream=None):
+               bucket_log2=0, polish_blocks=0, stats=True, key_type=None, stream=None):
     """Sorts every array of keys_list in place in one pass of the pipeline."""
     cnt = len(keys_list)
     kp = (C.c_void_p * cnt)(*[k.data_ptr() for k in keys_list])
@@ -242,7 +244,7 @@ def sort_batch(keys_list, models, payloads=None, *, m=1.25, eps=3, tau=1024, pre
         pp = (C.c_void_p * cnt)(*[0 if p is None else p.data_ptr() for p in payloads])
     ns = (C.c_uint64 * cnt)(*[k.numel() for k in keys_list])
     fs = (C.c_void_p * cnt)(*[mm.handle.value for mm in models])
-    o = _sopts(m, eps, tau, precision, bucket_log2, None, None, not stats)
+    o = _sopts(m, eps, tau, precision, bucket_log2, None, None, not stats, False, polish_blocks)
     st = (L.Stats * cnt)() if stats else None
     L.check("nnsort_sort_batch", L.lib().nnsort_sort_batch(
         kp, pp, ns, cnt, key_code(keys_list[0], key_type), fs, C.byref(o), st, _stream(stream)))

@@ -36,7 +36,7 @@ class SortOpts(C.Structure):
     _fields_ = [("m", C.c_float), ("eps", C.c_int32), ("tau", C.c_uint64),
                 ("precision", C.c_int32), ("bucket_log2", C.c_int32),
                 ("d_slots", C.c_void_p), ("d_fate", C.c_void_p), ("no_sync", C.c_int32),
-                ("timing", C.c_int32)]
+                ("timing", C.c_int32), ("polish_blocks", C.c_int32)]
 
 
 class Stats(C.Structure):

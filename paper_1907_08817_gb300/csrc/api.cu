@@ -751,7 +751,8 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     sa.err = L.err;
     sa.key_bytes = kb;
     sa.dtype = dtype;
-    sa.polish_cap = polish_capacity(kb, anypay, rows, P.wlog, 2, &sa.polish_smem);
+    const int pblocks = (o.polish_blocks >= 1 && o.polish_blocks <= 3) ? o.polish_blocks : 3;
+    sa.polish_cap = polish_capacity(kb, anypay, rows, P.wlog, pblocks, &sa.polish_smem);
     sa.allow_defer = 1;
     CK(launch_rounds(sa, s));
     CK(mark(4));

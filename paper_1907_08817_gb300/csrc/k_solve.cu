@@ -111,11 +111,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
     if (nbk <= (uint32_t)ROUND_CAP) {
         uint16_t ls[ROUND_ITEMS];
         uint8_t cur[ROUND_ITEMS];
+        W okey[ROUND_ITEMS];  // loaded with the positions, used after the rounds
 #pragma unroll
         for (int k = 0; k < ROUND_ITEMS; ++k) {
             const uint32_t i = k * SOLVE_THREADS + tid;
             cur[k] = 0;
             ls[k] = (i < nbk) ? (uint16_t)(a.gs[s0 + i] & wm) : 0;
+            okey[k] = (i < nbk) ? ldk<W>(a.keys, s0 + i) : (W)0;
         }
         for (int r = 0; r < eps; ++r) {
             for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) tbl[j] = EMPTY32;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
                 for (int r = 1; r <= eps; ++r) ge[r] += (c >= r);
                 if (c < eps) {
                     KMax x;
-                    x.k = ordbits(word64(ldk<W>(a.keys, s0 + i)), dt);
+                    x.k = ordbits(word64(okey[k]), dt);
                     x.tb = a.rows ? a.rows[s0 + i] : i;
                     x.valid = 1;
                     mx[c] = kmax(mx[c], x);
@@ -152,7 +154,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
         }
     } else {
         // bucket beyond the register-resident capacity: state lives in the global rank array
-        if (tid == 0) atomicAdd(&a.stats[sh_seg].oversized, 1u);
         for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) a.rank[s0 + i] = 0;
         __syncthreads();
         for (int r = 0; r < eps; ++r) {
@@ -240,54 +241,81 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_finalize(SolveArgs a) {
 // ---------------------------------------------------------------------------------------------
 // CTA-level building blocks on index lists
 
-// stable LSD radix sort of an index list by a 32- or 64-bit digit source, 8 bits per pass,
-// skipping passes whose digit is constant over the list. Returns the buffer holding the result.
-template <typename Idx, typename DigitFn>
-__device__ Idx *cta_radix_sort(Idx *src, Idx *dst, uint32_t cnt, int keybits, DigitFn digit,
-                               uint32_t *hist /*256*/, uint16_t *wcnt /*[SNW][256]*/,
-                               uint32_t *tot /*256*/, uint32_t *scratch /*33*/) {
+// Stable LSD radix sort of an index list by a 32- or 64-bit key (kf(x)), 8-bit digits. One sweep
+// builds the histograms of every digit; a digit that is constant over the list skips its pass.
+// A pass moves the list in tiles of SOLVE_THREADS * SORT_ITEMS elements: warp w ranks its 256
+// consecutive elements with match/popc over 8 rounds, the per-(digit, warp) counts become positions
+// with the running per-digit base folded in, and each element is written straight to its place.
+// Returns the buffer holding the result.
+constexpr int SORT_ITEMS = 8;
+constexpr uint32_t SORT_TILE = SOLVE_THREADS * SORT_ITEMS;
+template <typename Idx, typename KeyFn>
+__device__ Idx *cta_radix_sort(Idx *src, Idx *dst, uint32_t cnt, int keybits, KeyFn kf,
+                               uint32_t *hist /*[8][256]*/, uint32_t *wcnt /*[SNW][256]*/,
+                               uint32_t *scratch /*33*/) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    for (int shift = 0; shift < keybits; shift += 8) {
-        if (tid < 256) hist[tid] = 0;
-        __syncthreads();
-        for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) atomicAdd(&hist[digit(src[i], shift)], 1u);
-        __syncthreads();
-        const bool skip = cnt == 0 || hist[digit(src[0], shift)] == cnt;
-        __syncthreads();
-        if (skip) continue;
-        const uint32_t hv = (tid < 256) ? hist[tid] : 0u;
+    const int npass = keybits / 8;
+    for (int i = tid; i < npass * 256; i += SOLVE_THREADS) hist[i] = 0;
+    for (int i = tid; i < SNW * 256; i += SOLVE_THREADS) wcnt[i] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
+        const unsigned long long k = kf(src[i]);
+        for (int p = 0; p < npass; ++p) atomicAdd(&hist[p * 256 + (uint32_t)((k >> (8 * p)) & 0xFFu)], 1u);
+    }
+    __syncthreads();
+    if (cnt == 0) return src;
+    const unsigned long long kfirst = kf(src[0]);
+    for (int p = 0; p < npass; ++p) {
+        uint32_t *h = hist + p * 256;
+        const int shift = 8 * p;
+        if (h[(uint32_t)((kfirst >> shift) & 0xFFu)] == cnt) continue;  // same decision on every thread
+        const uint32_t hv = (tid < 256) ? h[tid] : 0u;
         const uint32_t ex = block_excl_sum(hv, scratch, nullptr);
-        if (tid < 256) {
-            hist[tid] = ex;  // running base per digit
-            for (int ww = 0; ww < SNW; ++ww) wcnt[ww * 256 + tid] = 0;
-        }
+        if (tid < 256) h[tid] = ex;  // running base per digit
         __syncthreads();
-        for (uint32_t t0 = 0; t0 < cnt; t0 += SOLVE_THREADS) {
-            const uint32_t i = t0 + tid;
-            const bool valid = i < cnt;
-            const Idx x = valid ? src[i] : (Idx)0;
-            const uint32_t d = valid ? digit(x, shift) : 0x1FFu;
-            const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-            const uint32_t wr = __popc(peers & lt);
-            if (valid && (peers & lt) == 0) wcnt[w * 256 + d] = (uint16_t)__popc(peers);
+        for (uint32_t t0 = 0; t0 < cnt; t0 += SORT_TILE) {
+            Idx x[SORT_ITEMS];
+            uint32_t d[SORT_ITEMS], wr[SORT_ITEMS];
+#pragma unroll
+            for (int r = 0; r < SORT_ITEMS; ++r) {
+                const uint32_t i = t0 + (uint32_t)w * (32 * SORT_ITEMS) + r * 32 + lane;
+                x[r] = (i < cnt) ? src[i] : (Idx)0;
+            }
+#pragma unroll
+            for (int r = 0; r < SORT_ITEMS; ++r) {
+                const uint32_t i = t0 + (uint32_t)w * (32 * SORT_ITEMS) + r * 32 + lane;
+                d[r] = (i < cnt) ? (uint32_t)((kf(x[r]) >> shift) & 0xFFu) : 0x1FFu;
+            }
+#pragma unroll
+            for (int r = 0; r < SORT_ITEMS; ++r) {
+                const bool valid = d[r] < 256u;
+                const unsigned peers = __match_any_sync(0xFFFFFFFFu, d[r]);
+                uint32_t c = 0;
+                if (valid) c = wcnt[w * 256 + d[r]];
+                __syncwarp();
+                if (valid) {
+                    wr[r] = c + __popc(peers & lt);
+                    if ((peers & lt) == 0) wcnt[w * 256 + d[r]] = c + __popc(peers);
+                }
+                __syncwarp();
+            }
             __syncthreads();
             if (tid < 256) {
-                uint32_t run = 0;
+                uint32_t run = h[tid];
                 for (int ww = 0; ww < SNW; ++ww) {
                     const uint32_t c = wcnt[ww * 256 + tid];
-                    wcnt[ww * 256 + tid] = (uint16_t)run;
+                    wcnt[ww * 256 + tid] = run;
                     run += c;
                 }
-                tot[tid] = run;
+                h[tid] = run;
             }
             __syncthreads();
-            if (valid) dst[hist[d] + wcnt[w * 256 + d] + wr] = x;
+#pragma unroll
+            for (int r = 0; r < SORT_ITEMS; ++r)
+                if (d[r] < 256u) dst[wcnt[w * 256 + d[r]] + wr[r]] = x[r];
             __syncthreads();
-            if (tid < 256) {
-                hist[tid] += tot[tid];
-                for (int ww = 0; ww < SNW; ++ww) wcnt[ww * 256 + tid] = 0;
-            }
+            for (int i = tid; i < SNW * 256; i += SOLVE_THREADS) wcnt[i] = 0;
             __syncthreads();
         }
         Idx *tmp = src; src = dst; dst = tmp;
@@ -317,9 +345,8 @@ __device__ void cta_merge(const Idx *A, uint32_t na, const Idx *B, uint32_t nb, 
 // ---------------------------------------------------------------------------------------------
 // k_polish
 struct PolishSmem {
-    uint32_t hist[256];
-    uint32_t tot[256];
-    uint16_t wcnt[SNW * 256];
+    uint32_t hist[8 * 256];
+    uint32_t wcnt[SNW * 256];
     uint32_t scratch[33];
     KMax kscratch[33];
     uint32_t rl_off[MAXR + 1];
@@ -433,8 +460,8 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
         if (v.F[i]) v.X[lo_++] = (Idx)i;
     __syncthreads();
     // QuickSort(w): stable radix sort by key (input order breaks ties, i.e. (key, row) order)
-    auto dig = [&](Idx x, int shift) -> uint32_t { return (uint32_t)((v.ok(x) >> shift) & 0xFFu); };
-    Idx *A = cta_radix_sort<Idx>(v.X, v.Y, nl, keybits, dig, sm.hist, sm.wcnt, sm.tot, sm.scratch);
+    auto kf = [&](Idx x) -> unsigned long long { return v.ok(x); };
+    Idx *A = cta_radix_sort<Idx>(v.X, v.Y, nl, keybits, kf, sm.hist, sm.wcnt, sm.scratch);
     Idx *Bf = (A == v.X) ? v.Y : v.X;
     __syncthreads();
     // polish: A' <- merge(A', R_i), i = 1..t
@@ -478,8 +505,8 @@ int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks
     const size_t fixed = sizeof(PolishSmem) + 256;
     const size_t tbl = ((size_t)4 << wlog);
     const size_t per = key_bytes + 2 + 1 + 1 + (payload ? 4 : 0) + (rows ? 4 : 0) + 3 * 2;
-    // shared memory per SM is 228 KB; each resident block also reserves 1 KB
-    const size_t budget = (blocks_per_sm <= 1 ? 226 : 226 / blocks_per_sm - 2) * 1024 - sizeof(PolishSmem);
+    // shared memory per SM is 228 KB (227 KB usable by one block); each resident block reserves 1 KB
+    const size_t budget = (blocks_per_sm <= 1) ? 227 * 1024 : (228 * 1024) / blocks_per_sm - 1024 - 512;
     long cap = (long)((budget - fixed - tbl) / per);
     cap = std::min<long>(cap, 65534);
     cap &= ~15L;
@@ -556,6 +583,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
                                   reinterpret_cast<uint16_t *>(TB), Wn - 1u, a.dtype};
         polish_bucket<W, uint16_t>(a, sm, v, b, s0, nbk, sg);
     } else {
+        if (tid == 0) atomicAdd(&a.stats[sm.seg].oversized, 1u);
         uint32_t *TB = reinterpret_cast<uint32_t *>(dyn);
         BucketView<W, uint32_t> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
                                   a.rank + s0, a.g_flag + s0, a.pay ? a.pay + s0 : nullptr,
@@ -670,15 +698,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam(SolveArgs a) {
     const uint32_t *rr = a.out_rows ? a.out_rows + sg.ebase + lo : nullptr;
     uint32_t *res = X;
     if (rr) {
-        auto rdig = [&](uint32_t x, int shift) -> uint32_t { return (rr[x] >> shift) & 0xFFu; };
-        res = cta_radix_sort<uint32_t>(X, Y, (uint32_t)len, 32, rdig, sm.hist, sm.wcnt, sm.tot, sm.scratch);
+        auto rkf = [&](uint32_t x) -> unsigned long long { return rr[x]; };
+        res = cta_radix_sort<uint32_t>(X, Y, (uint32_t)len, 32, rkf, sm.hist, sm.wcnt, sm.scratch);
     }
     uint32_t *oth = (res == X) ? Y : X;
-    auto kdig = [&](uint32_t x, int shift) -> uint32_t {
-        return (uint32_t)((ordbits(word64(rk[x]), dt) >> shift) & 0xFFu);
-    };
-    res = cta_radix_sort<uint32_t>(res, oth, (uint32_t)len, a.key_bytes * 8, kdig, sm.hist, sm.wcnt,
-                                   sm.tot, sm.scratch);
+    auto kkf = [&](uint32_t x) -> unsigned long long { return ordbits(word64(rk[x]), dt); };
+    res = cta_radix_sort<uint32_t>(res, oth, (uint32_t)len, a.key_bytes * 8, kkf, sm.hist, sm.wcnt,
+                                   sm.scratch);
     __syncthreads();
     // gather through scratch, then copy back
     W *tk = reinterpret_cast<W *>(a.key_scratch) + sg.ebase;
