@@ -99,6 +99,10 @@ typedef struct {
     uint32_t batch;    /* 0: full batch; otherwise samples per step drawn from the labelled set */
     float lr, beta1, beta2, adam_eps;
     uint64_t seed;     /* SplitMix64 stream for sampling, initialisation and mini-batches */
+    int32_t monotone;  /* 1: sign-structured weights (layer-1 unit j keeps the sign s_j of its
+                          initial input weight, output unit k the sign q_k of its initial output
+                          weight; W2_kj carries s_j q_k, or W3_j carries s_j with one hidden
+                          layer), projected after every Adam step, so f never decreases */
 } nnsort_train_opts;
 
 /* Sort options (Fig. "Algorithm NN-sort" inputs m, eps, tau). Defaults: m 1.25 (the paper's

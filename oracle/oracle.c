@@ -458,7 +458,30 @@ typedef struct {
     uint64_t batch;
     double lr, beta1, beta2, adam_eps;
     uint64_t seed;
+    int32_t monotone;
 } orc_train_opts;
+
+/* Monotone option: every path from the input to the output gets a non-negative weight product,
+ * so F is non-decreasing in x. Hidden unit j of layer 1 keeps the sign s_j of its initial input
+ * weight; with one hidden layer W3_j must carry s_j; with two, output unit k keeps the sign q_k of
+ * its initial W3_k and W2_kj must carry s_j q_k. sgn[i] is +1/-1 for constrained parameters and 0
+ * for free ones (biases). */
+void orc_monotone_signs(const orc_arch *a, const float *p0, double *sgn) {
+    const int H1 = a->h1, H2 = a->h2;
+    const uint64_t P = orc_num_params(a);
+    for (uint64_t i = 0; i < P; ++i) sgn[i] = 0.0;
+    for (int j = 0; j < H1; ++j) sgn[j] = (p0[j] >= 0.0f) ? 1.0 : -1.0;
+    if (a->layers == 1) {
+        for (int j = 0; j < H1; ++j) sgn[2 * H1 + j] = sgn[j];
+    } else {
+        const uint64_t w2 = 2 * (uint64_t)H1, w3 = w2 + (uint64_t)H2 * H1 + H2;
+        for (int k = 0; k < H2; ++k) {
+            const double q = (p0[w3 + k] >= 0.0f) ? 1.0 : -1.0;
+            sgn[w3 + k] = q;
+            for (int j = 0; j < H1; ++j) sgn[w2 + (uint64_t)k * H1 + j] = sgn[j] * q;
+        }
+    }
+}
 
 int orc_train(const void *keys, int dtype, uint64_t n, const orc_train_opts *o, orc_norm *norm_out,
               double *params_out, double *loss_hist) {
@@ -474,6 +497,13 @@ int orc_train(const void *keys, int dtype, uint64_t n, const orc_train_opts *o, 
     orc_init_params(&o->arch, o->seed, pf);
     double *m = (double *)calloc(P, sizeof(double)), *v = (double *)calloc(P, sizeof(double));
     double *g = (double *)malloc(P * sizeof(double));
+    double *sgn = (double *)calloc(P, sizeof(double));
+    if (o->monotone) {
+        /* initial weights take the required signs (magnitudes kept) */
+        orc_monotone_signs(&o->arch, pf, sgn);
+        for (uint64_t i = 0; i < P; ++i)
+            if (sgn[i] != 0.0) pf[i] = (float)(sgn[i] * fabs((double)pf[i]));
+    }
     for (uint64_t i = 0; i < P; ++i) params_out[i] = (double)pf[i];
     const uint64_t B = o->batch ? o->batch : S;
     double *xb = (double *)malloc(B * sizeof(double)), *lb = (double *)malloc(B * sizeof(double));
@@ -488,8 +518,11 @@ int orc_train(const void *keys, int dtype, uint64_t n, const orc_train_opts *o, 
                                                g, NULL);
         if (loss_hist) loss_hist[t] = L;
         orc_adam_f64(params_out, g, m, v, P, t + 1, o->lr, o->beta1, o->beta2, o->adam_eps);
+        if (o->monotone)  /* projection: a weight that crossed zero stops at zero */
+            for (uint64_t i = 0; i < P; ++i)
+                if (sgn[i] * params_out[i] < 0.0) params_out[i] = 0.0;
     }
-    free(xf); free(lf); free(pf); free(m); free(v); free(g); free(xb); free(lb);
+    free(xf); free(lf); free(pf); free(m); free(v); free(g); free(xb); free(lb); free(sgn);
     return 0;
 }
 

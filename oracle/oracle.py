@@ -47,7 +47,8 @@ class TrainOpts(C.Structure):
     _fields_ = [("arch", Arch), ("translate", C.c_int32), ("loss", C.c_int32),
                 ("huber_delta", C.c_double), ("sample_n", C.c_uint64), ("steps", C.c_uint64),
                 ("batch", C.c_uint64), ("lr", C.c_double), ("beta1", C.c_double),
-                ("beta2", C.c_double), ("adam_eps", C.c_double), ("seed", C.c_uint64)]
+                ("beta2", C.c_double), ("adam_eps", C.c_double), ("seed", C.c_uint64),
+                ("monotone", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -226,11 +227,11 @@ def sample_labels(keys: np.ndarray, S: int, seed: int, translate: int = ORDBITS)
 
 def train(keys: np.ndarray, layers=1, h1=32, h2=0, translate=ORDBITS, loss=MSE, huber_delta=0.01,
           sample_n=10_000, steps=100, batch=0, lr=1e-2, beta1=0.9, beta2=0.999, adam_eps=1e-8,
-          seed=0):
+          seed=0, monotone=False):
     """Binary64 training; returns (Model with params rounded to binary32, params f64, loss history)."""
     keys = np.ascontiguousarray(keys)
     o = TrainOpts(Arch(layers, h1, h2), translate, loss, huber_delta, sample_n, steps, batch, lr,
-                  beta1, beta2, adam_eps, seed)
+                  beta1, beta2, adam_eps, seed, 1 if monotone else 0)
     P = num_params(layers, h1, h2)
     p = np.empty(P, dtype=np.float64)
     hist = np.empty(max(steps, 1), dtype=np.float64)

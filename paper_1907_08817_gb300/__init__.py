@@ -143,12 +143,13 @@ def _topts(**kw) -> L.TrainOpts:
 
 def train(keys, *, key_type=None, layers=1, h1=32, h2=0, translate="ordbits", loss="mse",
           huber_delta=0.01, sample_n=10_000, steps=100, batch=0, lr=1e-2, beta1=0.9, beta2=0.999,
-          adam_eps=1e-8, seed=0, stream=None):
+          adam_eps=1e-8, seed=0, monotone=False, stream=None):
     """Trains f on the device from a seeded sample of `keys` (device tensor). Returns
     (Model, per-step loss history as numpy)."""
     o = _topts(layers=layers, h1=h1, h2=h2, translate=translate, loss=loss,
                huber_delta=huber_delta, sample_n=sample_n, steps=steps, batch=batch, lr=lr,
-               beta1=beta1, beta2=beta2, adam_eps=adam_eps, seed=seed)
+               beta1=beta1, beta2=beta2, adam_eps=adam_eps, seed=seed,
+               monotone=1 if monotone else 0)
     hist = np.zeros(max(steps, 1), dtype=np.float32)
     h = C.c_void_p()
     L.check("nnsort_train", L.lib().nnsort_train(

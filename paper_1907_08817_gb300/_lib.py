@@ -29,7 +29,7 @@ class TrainOpts(C.Structure):
                 ("translate", C.c_int32), ("loss", C.c_int32), ("huber_delta", C.c_float),
                 ("sample_n", C.c_uint64), ("steps", C.c_uint32), ("batch", C.c_uint32),
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("adam_eps", C.c_float), ("seed", C.c_uint64)]
+                ("adam_eps", C.c_float), ("seed", C.c_uint64), ("monotone", C.c_int32)]
 
 
 class SortOpts(C.Structure):

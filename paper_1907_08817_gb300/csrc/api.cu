@@ -1099,16 +1099,38 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     const int blocks = train_grad_blocks(B);
     // device buffers for this call (separate from the per-stream arena used by sampling)
     float *dx = nullptr;
-    const size_t fl = S * 2 + Pp * 4 + (size_t)blocks * Pp + blocks + std::max<uint32_t>(o.steps, 1) + 64;
+    const size_t fl = S * 2 + Pp * 5 + (size_t)blocks * Pp + blocks + std::max<uint32_t>(o.steps, 1) + 64;
     CK(cudaMallocAsync((void **)&dx, fl * sizeof(float), s));
     float *dlab = dx + S, *dp = dlab + S, *dm = dp + Pp, *dv = dm + Pp, *dg = dv + Pp;
-    float *dpart = dg + Pp, *dlp = dpart + (size_t)blocks * Pp, *dloss = dlp + blocks;
+    float *dmask = dg + Pp;
+    float *dpart = dmask + Pp, *dlp = dpart + (size_t)blocks * Pp, *dloss = dlp + blocks;
     nnsort_model_desc d;
     int rc = nnsort_sample_labels(d_keys, n, dtype, S, o.seed, o.translate, &d, dx, dlab, nullptr, s);
     if (rc) { cudaFreeAsync(dx, s); return rc; }
     d.layers = o.layers; d.h1 = o.h1; d.h2 = o.h2;
     std::vector<float> p0(P);
     init_params_host(o.layers, o.h1, o.h2, o.seed, p0.data());
+    std::vector<float> mask;
+    if (o.monotone) {
+        // sign structure: layer-1 unit j keeps sign s_j of W1_j; with two hidden layers output
+        // unit k keeps sign q_k of W3_k and W2_kj carries s_j q_k; with one, W3_j carries s_j
+        std::vector<float> sg(P, 0.0f);
+        for (int j = 0; j < o.h1; ++j) sg[j] = p0[j] >= 0.0f ? 1.0f : -1.0f;
+        if (o.layers == 1) {
+            for (int j = 0; j < o.h1; ++j) sg[2 * o.h1 + j] = sg[j];
+        } else {
+            const size_t w2 = 2 * (size_t)o.h1, w3 = w2 + (size_t)o.h2 * o.h1 + o.h2;
+            for (int k = 0; k < o.h2; ++k) {
+                const float q = p0[w3 + k] >= 0.0f ? 1.0f : -1.0f;
+                sg[w3 + k] = q;
+                for (int j = 0; j < o.h1; ++j) sg[w2 + (size_t)k * o.h1 + j] = sg[j] * q;
+            }
+        }
+        for (size_t u = 0; u < P; ++u)
+            if (sg[u] != 0.0f) p0[u] = sg[u] * std::fabs(p0[u]);
+        mask = to_padded(d, pa, sg.data());
+        CK(cudaMemcpyAsync(dmask, mask.data(), Pp * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
     const std::vector<float> pp = to_padded(d, pa, p0.data());
     CK(cudaMemcpyAsync(dp, pp.data(), Pp * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dm, 0, 2 * Pp * sizeof(float), s));
@@ -1117,6 +1139,7 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     t.loss_out = dloss; t.x = dx; t.label = dlab; t.S = S; t.batch = o.batch;
     t.batch_seed = rng_h(o.seed, TAG_BATCH); t.loss = o.loss; t.delta = o.huber_delta;
     t.lr = o.lr; t.b1 = o.beta1; t.b2 = o.beta2; t.eps = o.adam_eps; t.P = Pp;
+    t.mask = o.monotone ? dmask : nullptr;
     for (uint32_t k = 0; k < o.steps; ++k) {
         t.step = (int)k;
         CK(launch_train_step(pa, t, s));

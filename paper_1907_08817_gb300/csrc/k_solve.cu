@@ -56,9 +56,12 @@ template <typename W> __device__ __forceinline__ W ldk(const void *p, size_t i) 
 __device__ __forceinline__ KMax kmax_none() { KMax r; r.k = 0; r.tb = 0; r.valid = 0; return r; }
 
 // block reduction of an array of MAXR maxima (one per iteration); result in out[] on all threads
-__device__ void block_reduce_kmax_rounds(KMax *v, int eps, KMax *sm /*[SNW][MAXR]*/, KMax *out) {
+__device__ __forceinline__ void block_reduce_kmax_rounds(const KMax (&v)[MAXR], int eps,
+                                                         KMax *sm /*[SNW][MAXR]*/, KMax *out) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int r = 0; r < eps; ++r) {
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+        if (r >= eps) break;
         KMax x = v[r];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -142,13 +145,15 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
             if (i < nbk) {
                 const int c = cur[k] > eps ? eps : cur[k];
                 a.rank[s0 + i] = (uint8_t)c;
-                for (int r = 1; r <= eps; ++r) ge[r] += (c >= r);
-                if (c < eps) {
-                    KMax x;
-                    x.k = ordbits(word64(okey[k]), dt);
-                    x.tb = a.rows ? a.rows[s0 + i] : i;
-                    x.valid = 1;
-                    mx[c] = kmax(mx[c], x);
+                KMax x;
+                x.k = ordbits(word64(okey[k]), dt);
+                x.tb = a.rows ? a.rows[s0 + i] : i;
+                x.valid = 1;
+                // compile-time round indices keep the per-round state in registers
+#pragma unroll
+                for (int r = 0; r < MAXR; ++r) {
+                    ge[r + 1] += (r + 1 <= eps && c >= r + 1) ? 1u : 0u;
+                    if (c == r && r < eps) mx[r] = kmax(mx[r], x);
                 }
             }
         }
@@ -172,18 +177,21 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
         }
         for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) {
             const int c = a.rank[s0 + i];
-            for (int r = 1; r <= eps; ++r) ge[r] += (c >= r);
-            if (c < eps) {
-                KMax x;
-                x.k = ordbits(word64(ldk<W>(a.keys, s0 + i)), dt);
-                x.tb = a.rows ? a.rows[s0 + i] : i;
-                x.valid = 1;
-                mx[c] = kmax(mx[c], x);
+            KMax x;
+            x.k = ordbits(word64(ldk<W>(a.keys, s0 + i)), dt);
+            x.tb = a.rows ? a.rows[s0 + i] : i;
+            x.valid = 1;
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                ge[r + 1] += (r + 1 <= eps && c >= r + 1) ? 1u : 0u;
+                if (c == r && r < eps) mx[r] = kmax(mx[r], x);
             }
         }
     }
     // totals
-    for (int r = 1; r <= eps; ++r) {
+#pragma unroll
+    for (int r = 1; r <= MAXR; ++r) {
+        if (r > eps) break;
         const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, ge[r]);
         if ((tid & 31) == 0 && v) atomicAdd(&cge[r], v);
     }

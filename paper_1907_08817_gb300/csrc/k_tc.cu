@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
             if (a.row_init) a.row_init[e] = (uint32_t)i;
             if (a.slots_out) a.slots_out[e] = slot;
             if (a.y_out) a.y_out[e] = y;
-            for (int p = 0; p < npass; ++p) {
+#pragma unroll
+            for (int p = 0; p < MAX_PASSES; ++p) {
+                if (p >= npass) break;
                 const uint32_t d = (g >> a.plan.shift[p]) & ((1u << a.plan.bits[p]) - 1u);
                 atomicAdd(&sh_hist[p * RADIX_BINS + d], 1u);
             }

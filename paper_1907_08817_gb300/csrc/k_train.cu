@@ -521,6 +521,7 @@ struct ReduceArgs {
     float loss_scale;
     // Adam
     float *params, *m, *v;
+    const float *mask;  // nullable: +1/-1 sign a parameter must keep, 0 free
     float lr, b1, b2, eps, c1, c2;
 };
 
@@ -541,7 +542,9 @@ __global__ void k_reduce(ReduceArgs r) {
         r.m[p] = m;
         r.v[p] = v;
         const float mh = m / r.c1, vh = v / r.c2;
-        r.params[p] -= r.lr * mh / (sqrtf(vh) + r.eps);
+        float np = r.params[p] - r.lr * mh / (sqrtf(vh) + r.eps);
+        if (r.mask && r.mask[p] * np < 0.0f) np = 0.0f;  // monotone projection
+        r.params[p] = np;
     }
 }
 
@@ -569,6 +572,7 @@ cudaError_t launch_train_step(const PadArch &a, const TrainStepArgs &t, cudaStre
     r.partials = t.partials; r.blocks = blocks; r.P = t.P; r.out = t.grad;
     r.loss_partials = t.loss_partials; r.loss_out = t.loss_out + t.step; r.loss_scale = 1.0f / (float)B;
     r.params = t.params; r.m = t.m; r.v = t.v; r.lr = t.lr; r.b1 = t.b1; r.b2 = t.b2; r.eps = t.eps;
+    r.mask = t.mask;
     const double c1 = 1.0 - std::pow((double)t.b1, (double)(t.step + 1));
     const double c2 = 1.0 - std::pow((double)t.b2, (double)(t.step + 1));
     r.c1 = (float)c1; r.c2 = (float)c2;

@@ -113,6 +113,33 @@ def test_device_training_tracks_binary64_training(cfg):
     assert hist[-1] < hist[0]
 
 
+@pytest.mark.parametrize("arch", [(1, 16, 0), (2, 32, 32), (2, 64, 64)])
+def test_monotone_training_on_device(arch):
+    """Sign-structured training: the device run follows the oracle's projected binary64 run, and
+    the resulting positions never decrease with the key, in binary32 and BF16 arithmetic, so the
+    polish finds no out-of-order element and no bucket seam needs repair."""
+    layers, h1, h2 = arch
+    keys = W.lognormal_dup_f32(2_000_000, 12, sigma=2.0)
+    dk, _ = to_dev(keys)
+    cfg = dict(layers=layers, h1=h1, h2=h2, translate=orc.ORDBITS, sample_n=20_000, steps=100,
+               batch=4096, seed=4)
+    model, hist = nns.train(dk, lr=1e-2, monotone=True, **cfg)
+    om, p64, ohist = orc.train(keys, lr=1e-2, monotone=True, **cfg)
+    np.testing.assert_allclose(hist, ohist, rtol=5e-3, atol=1e-6)
+    _, p = model.describe()
+    assert np.max(np.abs(p - p64)) <= 5e-3 * np.abs(p64).max()
+    precs = ["fp32"] + (["bf16"] if layers == 2 else [])
+    for prec in precs:
+        k = dk.clone()
+        slots, _ = nns.predict(k, model, precision=prec, want_y=False)
+        order = torch.argsort(k, stable=True)
+        s_sorted = slots[order]
+        assert bool((s_sorted[1:] >= s_sorted[:-1]).all())
+        st = nns.sort(k, None, model, precision=prec)
+        assert sum(st["out_of_order"]) == 0 and st["repaired"] == 0
+        assert torch.equal(k, torch.sort(dk).values)
+
+
 def test_trained_model_gains_over_untrained_and_linear():
     """What the learned network buys: fewer conflicts and a smaller traditional-sort share than the
     same pipeline with the untrained network or with the plain min-max (linear) map."""
