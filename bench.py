@@ -159,6 +159,45 @@ def reference_arm(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- serving leg
+SERVE_TRAIN = dict(layers=2, h1=32, h2=32, sample_n=20_000, steps=100, batch=4096, lr=1e-2)
+
+
+def serving_leg(nns, W, count=200, rate=400.0, seed=5):
+    """Poisson arrivals of float64 requests (log-uniform 10K..4M keys; uniform / lognormal(0,2) /
+    clustered), per-request device-trained 1-32-32-1, 120 GiB admission budget. Continuous
+    batching (2 worker streams, up to 16 requests per batch) against FIFO (1 worker, 1 request
+    per batch). Latency: submit -> sorted result back in host memory."""
+    reqs = W.serving_requests(count=count, seed=seed, lo=10_000, hi=4_000_000, rate_per_s=rate)
+    out = {}
+    for mode, kw in (("continuous_batching", dict(workers=2, max_batch=16)),
+                     ("fifo", dict(workers=1, max_batch=1))):
+        arrays = [r["keys"].copy() for r in reqs]
+        lats = []
+        with nns.Server(hbm_budget=120 << 30, train=SERVE_TRAIN, **kw) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for i, r in enumerate(reqs):
+                dt = r["arrival_s"] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(arrays[i], seed=i))
+            for t in tickets:
+                _, lat = srv.wait(t)
+                lats.append(lat)
+            wall = time.perf_counter() - t0
+        keys = sum(r["keys"].shape[0] for r in reqs)
+        for i in range(0, count, max(1, count // 8)):
+            assert np.all(arrays[i][1:] >= arrays[i][:-1])
+        out[mode] = {"p50_ms": 1e3 * float(np.percentile(lats, 50)),
+                     "p99_ms": 1e3 * float(np.percentile(lats, 99)),
+                     "mkeys_s": keys / wall / 1e6, "wall_s": wall}
+    out["requests"] = count
+    out["offered_rate_per_s"] = rate
+    out["keys"] = int(sum(r["keys"].shape[0] for r in reqs))
+    return out
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_job(nns, keys, precision, stats=True):
     model, hist = nns.train(keys, **ARCH, **TRAIN)
@@ -176,6 +215,7 @@ def main():
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -327,6 +367,10 @@ def main():
         e2e = {"value": n / statistics.median(tt) / 1e6, "unit": "Mkeys/s",
                "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb}
 
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = serving_leg(nns, W)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         ncpu = 300_000
@@ -351,7 +395,8 @@ def main():
                           "e": st["e"], "trad_rate": st["trad_rate"], "buckets": st["buckets"],
                           "oversized_buckets": st["oversized_buckets"], "repaired": st["repaired"],
                           "final_train_loss": float(hist[-1])},
-                "plain": plain, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "plain": plain, "serving": serving, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk.summary(),
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
 

@@ -237,6 +237,47 @@ int nnsort_sort_batch(void *const *d_keys, int32_t *const *d_payloads, const uin
                       int32_t count, int32_t dtype, const nnsort_model *const *fs,
                       const nnsort_sort_opts *o, nnsort_stats *st, cudaStream_t stream);
 
+/* ---- serving: continuous batching of sort requests ------------------------------------ */
+/* A server owns `workers` CUDA streams on the current device and a host scheduler thread.
+ * Requests (host arrays) are admitted in arrival order while the device memory they need fits
+ * the HBM budget; admitted requests wait in a queue that every idle worker drains into its next
+ * batch (up to max_batch requests or max_batch_keys keys), so requests that arrive while other
+ * batches run join the following batch and work on different streams overlaps on the device.
+ * Per batch a worker copies the requests in, trains each request's model on the device
+ * (nnsort_train with `train` options and a per-request seed), sorts all of them with one
+ * nnsort_sort_batch call (`sort` options), and copies the results back into the caller's host
+ * arrays. Latency is measured from submit to the result being in host memory. The paper has no
+ * serving layer; this is the batched, served form of its method. */
+typedef struct {
+    size_t hbm_budget;          /* bytes of device memory admitted requests may hold */
+    int32_t workers;            /* streams / batches in flight (1 .. 8) */
+    int32_t max_batch;          /* requests per batch (>= 1); 1 makes the server FIFO */
+    uint64_t max_batch_keys;    /* keys per batch (0: unlimited) */
+    nnsort_train_opts train;    /* per-request training (seed is replaced by request seed) */
+    nnsort_sort_opts sort;      /* sort options (no injected positions, no trace) */
+} nnsort_server_opts;
+
+typedef struct nnsort_server nnsort_server;
+
+#define NNSORT_PENDING 1  /* status of nnsort_server_poll for a request not finished yet */
+
+/* Defaults: 120 GiB budget, 2 workers, max_batch 32, no key limit, default train/sort options. */
+void nnsort_default_server_opts(nnsort_server_opts *o);
+int nnsort_server_create(const nnsort_server_opts *o, nnsort_server **out);
+/* Queues one request. h_keys[n] (and h_payload[n], nullable) are host arrays the caller keeps
+ * alive and untouched until the request completes; they receive the sorted result in place.
+ * `seed` seeds the request's training. Returns NNSORT_E_BUDGET if the request alone exceeds the
+ * budget. *ticket identifies the request. Thread-safe. */
+int nnsort_server_submit(nnsort_server *srv, void *h_keys, int32_t *h_payload, uint64_t n,
+                         int32_t dtype, uint64_t seed, uint64_t *ticket);
+/* NNSORT_OK once the request finished (st, latency_s filled when not null; the ticket is then
+ * retired), NNSORT_PENDING before, NNSORT_E_STATE for an unknown ticket, or the request's error. */
+int nnsort_server_poll(nnsort_server *srv, uint64_t ticket, nnsort_stats *st, double *latency_s);
+/* As poll, but waits until the request finished. */
+int nnsort_server_wait(nnsort_server *srv, uint64_t ticket, nnsort_stats *st, double *latency_s);
+/* Finishes queued work, stops the workers and frees everything. */
+int nnsort_server_destroy(nnsort_server *srv);
+
 /* ---- sorting without device allocation ------------------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that cannot allocate
  * device memory when they sort: code whose memory budget was fixed up front, code that must not

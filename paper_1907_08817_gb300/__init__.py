@@ -320,3 +320,66 @@ class _LazyFn:
 
 
 NNSortMLPFunction = _LazyFn()
+
+
+# ------------------------------------------------------------------------------- serving
+class Server:
+    """Continuous-batching sort server (nnsort_server_*): host arrays in, sorted in place."""
+
+    def __init__(self, hbm_budget: int = 120 << 30, workers: int = 2, max_batch: int = 32,
+                 max_batch_keys: int = 0, train: dict | None = None, sort: dict | None = None):
+        SL = L.server_lib()
+        o = L.ServerOpts()
+        SL.nnsort_default_server_opts(C.byref(o))
+        o.hbm_budget, o.workers, o.max_batch, o.max_batch_keys = hbm_budget, workers, max_batch, max_batch_keys
+        o.train = _topts(**(train or {}))
+        so = dict(m=1.25, eps=3, tau=1024, precision="fp32", bucket_log2=0)
+        so.update(sort or {})
+        o.sort = _sopts(so["m"], so["eps"], so["tau"], so["precision"], so["bucket_log2"], None, None,
+                        False, False, so.get("polish_blocks", 0))
+        self._h = C.c_void_p()
+        L.check("nnsort_server_create", SL.nnsort_server_create(C.byref(o), C.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, keys: np.ndarray, payload: np.ndarray | None = None, seed: int = 0) -> int:
+        code = {np.dtype(np.float32): F32, np.dtype(np.float64): F64, np.dtype(np.uint32): U32,
+                np.dtype(np.uint64): U64}[keys.dtype]
+        assert keys.flags.c_contiguous and (payload is None or payload.flags.c_contiguous)
+        t = C.c_uint64()
+        L.check("nnsort_server_submit", L.lib().nnsort_server_submit(
+            self._h, keys.ctypes.data_as(C.c_void_p),
+            None if payload is None else payload.ctypes.data_as(C.c_void_p), keys.shape[0], code,
+            seed, C.byref(t)))
+        self._keep[t.value] = (keys, payload)
+        return t.value
+
+    def _result(self, fn, ticket):
+        st = L.Stats()
+        lat = C.c_double()
+        rc = fn(self._h, ticket, C.byref(st), C.byref(lat))
+        if rc == L.PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        L.check("nnsort_server_result", rc)
+        return st.as_dict(), lat.value
+
+    def poll(self, ticket: int):
+        """(stats, latency_s) once finished, else None."""
+        return self._result(L.lib().nnsort_server_poll, ticket)
+
+    def wait(self, ticket: int):
+        return self._result(L.lib().nnsort_server_wait, ticket)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().nnsort_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        self.close()

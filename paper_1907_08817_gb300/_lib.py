@@ -136,4 +136,32 @@ def exported_symbols() -> list[str]:
             "nnsort_model_save", "nnsort_model_load", "nnsort_sample_labels", "nnsort_train",
             "nnsort_mlp_forward", "nnsort_mlp_backward", "nnsort_mlp_loss_grad",
             "nnsort_predict", "nnsort_sort", "nnsort_sort_host", "nnsort_sort_batch",
-            "nnsort_train_sort_host", "nnsort_launch_count", "nnsort_sort_noalloc"]
+            "nnsort_train_sort_host", "nnsort_launch_count", "nnsort_sort_noalloc",
+            "nnsort_default_server_opts", "nnsort_server_create", "nnsort_server_submit",
+            "nnsort_server_poll", "nnsort_server_wait", "nnsort_server_destroy"]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("workers", C.c_int32), ("max_batch", C.c_int32),
+                ("max_batch_keys", C.c_uint64), ("train", TrainOpts), ("sort", SortOpts)]
+
+
+PENDING = 1
+SERVER_SIGS = {
+    "nnsort_default_server_opts": (None, [C.c_void_p]),
+    "nnsort_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nnsort_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_int32,
+                                       C.c_uint64, C.c_void_p]),
+    "nnsort_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "nnsort_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "nnsort_server_destroy": (C.c_int, [C.c_void_p]),
+}
+
+
+def server_lib():
+    L = lib()
+    for name, (res, args) in SERVER_SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
