@@ -62,8 +62,12 @@ typedef enum { NNSORT_TRANSLATE_ORDBITS = 0, NNSORT_TRANSLATE_VALUE = 1 } nnsort
 
 /* Arithmetic of the model's forward pass inside a sort. FP32: binary32 FMA chains, bit-identical
  * to the CPU reference. BF16: the hidden-to-hidden layer runs on the tensor cores (tcgen05, BF16
- * operands, FP32 accumulation); first and output layers stay binary32. */
-typedef enum { NNSORT_PREC_FP32 = 0, NNSORT_PREC_BF16 = 1 } nnsort_precision;
+ * operands, FP32 accumulation); first and output layers stay binary32. BF16X2: as BF16, but each
+ * first-layer activation h is passed as the pair hi = bf16(h), lo = bf16(h - hi), both multiplied
+ * by the BF16 weights into the same FP32 accumulator (two MMAs): the activations keep ~16
+ * significant bits, so F stays as finely resolved in x as the binary32 model (the weights'
+ * rounding only changes f smoothly). Two-hidden-layer models only; others use binary32. */
+typedef enum { NNSORT_PREC_FP32 = 0, NNSORT_PREC_BF16 = 1, NNSORT_PREC_BF16X2 = 2 } nnsort_precision;
 
 /* Training loss: mean squared error, or the Huber loss of Eq. (loss). */
 typedef enum { NNSORT_LOSS_MSE = 0, NNSORT_LOSS_HUBER = 1 } nnsort_loss;
@@ -146,6 +150,7 @@ typedef struct {
     float ms_stage[8];
     uint32_t partition_passes;                 /* stable partition passes run */
     uint32_t bucket_log2;                      /* log2 of the positions per bucket */
+    uint64_t repair_ranges;                    /* disjoint output ranges re-sorted across seams */
 } nnsort_stats;
 
 /* ---- library ---------------------------------------------------------------------------- */
@@ -210,7 +215,7 @@ int nnsort_mlp_loss_grad(const float *d_params, int32_t layers, int32_t h1, int3
 /* ---- the sort ----------------------------------------------------------------------------- */
 /* Lines 1 and 5-7 of Fig. "Algorithm NN-sort" alone: translate, model forward and the position
  * round(f(x) * n * m) clamped to [0, floor(n m)], for each of d_keys[n]. d_slots and d_y
- * (F(x) before rounding) are nullable outputs. `precision` selects FP32 or BF16 arithmetic. */
+ * (F(x) before rounding) are nullable outputs. `precision` selects the nnsort_precision arithmetic. */
 int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_model *f, float m,
                    int32_t precision, uint32_t *d_slots, float *d_y, cudaStream_t stream);
 /* The whole method on device arrays, in place: d_keys[n] (and d_payload[n] when not null) are

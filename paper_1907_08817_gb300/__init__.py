@@ -62,7 +62,7 @@ def _ptr(t):
 def _prec(p) -> int:
     if isinstance(p, int):
         return p
-    return {"fp32": PREC_FP32, "bf16": PREC_BF16}[p]
+    return {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16x2": L.PREC_BF16X2}[p]
 
 
 def _tr(t) -> int:
@@ -86,6 +86,15 @@ class Model:
     @property
     def handle(self) -> C.c_void_p:
         return self._h
+
+    @property
+    def shape(self) -> tuple:
+        """(layers, h1, h2) of the MLP."""
+        if getattr(self, "_shape", None) is None:
+            d = L.ModelDesc()
+            L.check("nnsort_model_describe", L.lib().nnsort_model_describe(self._h, C.byref(d), None))
+            self._shape = (d.layers, d.h1, d.h2)
+        return self._shape
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -199,13 +208,29 @@ def _sopts(m, eps, tau, precision, bucket_log2, slots, fate, no_sync, timing=Fal
     return o
 
 
+def _tuned(model, n, dtype, precision, eps, bucket_log2, polish_blocks):
+    """Fills the parameters left to the library (bucket_log2=0, polish_blocks=0, eps='auto') from
+    the autotuner's table for this key type, size class, model shape and precision."""
+    if model is None or (bucket_log2 and polish_blocks and eps != "auto"):
+        return (3 if eps == "auto" else eps), bucket_log2, polish_blocks
+    from . import autotune
+    t = autotune.tuned_options(dtype, n, *model.shape, precision)
+    return (t["eps"] if eps == "auto" else eps, bucket_log2 or t["bucket_log2"],
+            polish_blocks or t["polish_blocks"])
+
+
 def sort(keys, payload=None, model: Model | None = None, *, m=1.25, eps=3, tau=1024,
          precision="fp32", bucket_log2=0, slots=None, fate: bool = False, stats: bool = True,
          timing: bool = False, polish_blocks: int = 0, key_type=None, stream=None):
     """NN-sort in place. `slots` (int32 device tensor of positions) replaces the model.
+    bucket_log2=0 / polish_blocks=0 / eps='auto' take the autotuned setting for this workload
+    class (the library's defaults where none was tuned).
     Returns the stats dict (or None), plus the per-row fate tensor when fate=True."""
     torch = _torch()
     n = keys.numel()
+    eps, bucket_log2, polish_blocks = _tuned(None if slots is not None else model, n,
+                                             key_code(keys, key_type), precision, eps,
+                                             bucket_log2, polish_blocks)
     ft = torch.zeros(n, dtype=torch.int8, device=keys.device) if fate else None
     o = _sopts(m, eps, tau, precision, bucket_log2, slots, ft, not stats, timing, polish_blocks)
     st = L.Stats() if (stats or timing) else None
@@ -237,8 +262,13 @@ def sort_host(keys: np.ndarray, payload: np.ndarray | None = None, model: Model 
 
 def sort_batch(keys_list, models, payloads=None, *, m=1.25, eps=3, tau=1024, precision="fp32",
                bucket_log2=0, polish_blocks=0, stats=True, key_type=None, stream=None):
-    """Sorts every array of keys_list in place in one pass of the pipeline."""
+    """Sorts every array of keys_list in place in one pass of the pipeline (tuned parameters are
+    looked up for the mean array size and the first model's shape)."""
     cnt = len(keys_list)
+    if cnt:
+        eps, bucket_log2, polish_blocks = _tuned(
+            models[0], sum(k.numel() for k in keys_list) // cnt, key_code(keys_list[0], key_type),
+            precision, eps, bucket_log2, polish_blocks)
     kp = (C.c_void_p * cnt)(*[k.data_ptr() for k in keys_list])
     pp = None
     if payloads is not None:

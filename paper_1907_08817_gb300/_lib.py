@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libnnsort.so")
 MAX_ROUNDS = 8
 F32, F64, U32, U64 = 0, 1, 2, 3
 ORDBITS, VALUE = 0, 1
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
 LOSS_MSE, LOSS_HUBER = 0, 1
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "NaN key", -3: "out of memory",
@@ -49,7 +49,7 @@ class Stats(C.Structure):
                 ("trad_rate", C.c_double), ("buckets", C.c_uint64),
                 ("oversized_buckets", C.c_uint64), ("repaired", C.c_uint64),
                 ("ms_stage", C.c_float * 8), ("partition_passes", C.c_uint32),
-                ("bucket_log2", C.c_uint32)]
+                ("bucket_log2", C.c_uint32), ("repair_ranges", C.c_uint64)]
 
     def as_dict(self) -> dict:
         t = self.rounds
@@ -61,7 +61,8 @@ class Stats(C.Structure):
                 "e": [self.e[i] for i in range(t)], "trad_rate": self.trad_rate,
                 "buckets": self.buckets, "oversized_buckets": self.oversized_buckets,
                 "repaired": self.repaired, "ms_stage": [self.ms_stage[i] for i in range(8)],
-                "partition_passes": self.partition_passes, "bucket_log2": self.bucket_log2}
+                "partition_passes": self.partition_passes, "bucket_log2": self.bucket_log2,
+                "repair_ranges": self.repair_ranges}
 
 
 class NNSortError(RuntimeError):

@@ -438,6 +438,7 @@ struct Layout {
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2]; uint32_t *row[2]; uint32_t *out_rows;
     uint8_t *rank; uint8_t *g_flag; uint32_t *g_x, *g_y, *g_r; uint32_t *bstart;
     OKey *bmax, *carry, *blo, *bhi;
+    SeamRange *ranges; uint32_t *seam_cnt;
 };
 
 Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, bool pay, bool rows,
@@ -468,6 +469,8 @@ Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, boo
     L.carry = c.take<OKey>((size_t)NB * MAXR);
     L.blo = c.take<OKey>(NB);
     L.bhi = c.take<OKey>(NB);
+    L.ranges = c.take<SeamRange>((size_t)NB + nseg);
+    L.seam_cnt = c.take<uint32_t>(4);
     *total = align_up(c.off, 256);
     return L;
 }
@@ -570,35 +573,50 @@ void fill_stats(const Seg &s, const SegStats &d, nnsort_stats *st) {
     st->buckets = s.nb;
     st->oversized_buckets = d.oversized;
     st->repaired = d.repaired;
+    st->repair_ranges = d.ranges;
 }
 
-// stable multi-block radix sort by key of out[lo, hi) of one array, through the (now free)
-// partition buffers; used for seam repairs too large for one block
-int global_repair(Workspace *w, Layout &L, const Seg &sg, uint64_t lo, uint64_t hi, int kb, int dtype,
-                  cudaStream_t s) {
-    const uint64_t len = hi - lo;
-    if (len < 2) return NNSORT_OK;
-    const int npass = kb;  // 8-bit digits of the key's order image
-    unsigned char *keys = reinterpret_cast<unsigned char *>(sg.keys) + lo * kb;
-    uint32_t *pay = sg.payload ? reinterpret_cast<uint32_t *>(sg.payload + lo) : nullptr;
-    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
-    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
-    CK(launch_key_hist(keys, len, kb, dtype, npass, L.hist, s));
-    CK(launch_digit_bases(L.hist, L.bases, npass, s));
-    for (int p = 0; p < npass; ++p) {
-        const int si = p & 1, di = si ^ 1;
+// the long seam ranges hr[0..nr) (host copy), sorted together: packed in output order into the
+// (now free) partition buffers key[0] / pay[0], stable multi-block radix sort by key, then (when
+// the ranges belong to more than one array) by array index, unpacked. `hp` is pinned staging for
+// the array-index histograms.
+int repair_long_ranges(Workspace *w, Layout &L, SeamRange *hr, uint32_t nr, int nseg, int kb,
+                       int dtype, bool anypay, uint32_t *hp, cudaStream_t s) {
+    std::sort(hr, hr + nr, [](const SeamRange &x, const SeamRange &y) {
+        return x.seg != y.seg ? x.seg < y.seg : x.lo < y.lo;
+    });
+    uint64_t total = 0;
+    for (uint32_t j = 0; j < nr; ++j) {
+        hr[j].pad = (uint32_t)total;
+        total += hr[j].hi - hr[j].lo;
+    }
+    if (total < 2) return NNSORT_OK;
+    const bool multi = hr[0].seg != hr[nr - 1].seg;
+    CK(cudaMemcpyAsync(L.ranges, hr, sizeof(SeamRange) * nr, cudaMemcpyHostToDevice, s));
+    uint32_t *pay0 = anypay ? L.pay[0] : nullptr;
+    const int sms = sm_count();
+    CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, L.key[0], pay0, multi ? L.gs[0] : nullptr,
+                        0, sms, s));
+    auto pass = [&](int p, int si, bool keydig, int shift, int bits, const uint32_t *base) -> int {
+        const int di = si ^ 1;
         OnesweepArgs a{};
-        a.N = len;
-        a.key_in = p == 0 ? (void *)keys : L.key[si];
+        a.N = total;
+        a.key_in = L.key[si];
         a.key_out = L.key[di];
-        if (pay) {
-            a.pay_in = p == 0 ? pay : L.pay[si];
+        if (pay0) {
+            a.pay_in = L.pay[si];
             a.pay_out = L.pay[di];
         }
-        a.key_digits = 1;
-        a.shift = 8 * p;
-        a.bits = 8;
-        a.digit_base = L.bases + p * RADIX_BINS;
+        if (keydig) {
+            if (multi) { a.row_in = L.gs[si]; a.row_out = L.gs[di]; }
+        } else {
+            a.gs_in = L.gs[si];
+            a.gs_out = L.gs[di];
+        }
+        a.key_digits = keydig ? 1 : 0;
+        a.shift = shift;
+        a.bits = bits;
+        a.digit_base = base;
         a.lookback = w->lookback;
         a.ticket = L.tickets + p * 4;
         a.epoch = next_epoch(w, s);
@@ -606,11 +624,42 @@ int global_repair(Workspace *w, Layout &L, const Seg &sg, uint64_t lo, uint64_t 
         a.key_bytes = kb;
         a.dtype = dtype;
         CK(launch_onesweep(a, s));
+        return NNSORT_OK;
+    };
+    int rc;
+    const int npass = kb;  // 8-bit digits of the key's order image; even, so the result ends in key[0]
+    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
+    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
+    CK(launch_key_hist(L.key[0], total, kb, dtype, npass, L.hist, s));
+    CK(launch_digit_bases(L.hist, L.bases, npass, s));
+    for (int p = 0; p < npass; ++p)
+        if ((rc = pass(p, p & 1, true, 8 * p, 8, L.bases + p * RADIX_BINS))) return rc;
+    int fin = 0;
+    if (multi) {
+        // array-index passes of at most 9 bits; their histograms come from the ranges' lengths
+        int sbits = 1;
+        while ((1u << sbits) < (uint32_t)nseg) ++sbits;
+        const int nsp = (sbits + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
+        std::memset(hp, 0, sizeof(uint32_t) * 4 * RADIX_BINS);
+        int sh[4], bt[4];
+        for (int q = 0, at = 0; q < nsp; ++q) {
+            bt[q] = (sbits - at + (nsp - q) - 1) / (nsp - q);
+            sh[q] = at;
+            at += bt[q];
+            for (uint32_t j = 0; j < nr; ++j)
+                hp[q * RADIX_BINS + ((hr[j].seg >> sh[q]) & ((1u << bt[q]) - 1u))] +=
+                    (uint32_t)(hr[j].hi - hr[j].lo);
+        }
+        CK(cudaMemcpyAsync(L.hist, hp, sizeof(uint32_t) * nsp * RADIX_BINS, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
+        CK(launch_digit_bases(L.hist, L.bases, nsp, s));
+        for (int q = 0; q < nsp; ++q)
+            if ((rc = pass(q, q & 1, false, sh[q], bt[q], L.bases + q * RADIX_BINS))) return rc;
+        fin = nsp & 1;
     }
-    const int fi = npass & 1;
-    CK(cudaMemcpyAsync(keys, L.key[fi], len * kb, cudaMemcpyDeviceToDevice, s));
-    if (pay) CK(cudaMemcpyAsync(pay, L.pay[fi], len * 4, cudaMemcpyDeviceToDevice, s));
-    return NNSORT_OK;
+    CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, L.key[fin], anypay ? L.pay[fin] : nullptr,
+                        nullptr, 1, sms, s));
+    return NNSORT_OK;  // the next call on this stream waits before it rewrites the staging area
 }
 
 int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype, nnsort_stats *st,
@@ -619,7 +668,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     if (op) o = *op; else nnsort_default_sort_opts(&o);
     if (!dtype_ok(dtype)) return NNSORT_E_INVALID_ARG;
     if (!(o.m > 0.0f) || o.eps < 0 || o.eps > NNSORT_MAX_ROUNDS) return NNSORT_E_INVALID_ARG;
-    if (o.precision != NNSORT_PREC_FP32 && o.precision != NNSORT_PREC_BF16) return NNSORT_E_INVALID_ARG;
+    if (o.precision < NNSORT_PREC_FP32 || o.precision > NNSORT_PREC_BF16X2) return NNSORT_E_INVALID_ARG;
     if (in.size() > 1 && (o.d_slots || o.d_fate)) return NNSORT_E_INVALID_ARG;
     const nnsort_model *f0 = nullptr;
     bool anypay = false;
@@ -649,7 +698,13 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     if ((rc = ensure_arena(w, need, s))) return rc;
     const uint64_t ptiles = (P.N + PART_TILE - 1) / PART_TILE;
     if ((rc = ensure_lookback(w, ptiles * RADIX_BINS, s))) return rc;
-    const size_t pin_need = sizeof(Seg) * nseg + sizeof(SegStats) * nseg + 256;
+    // staging: the segment table, then the statistics, the seam counters and the long seam ranges
+    // (disjoint and longer than SEAM_CTA_MAX each, so at most N / SEAM_CTA_MAX of them)
+    const size_t pin_stats = align_up(sizeof(Seg) * nseg, 64);
+    const size_t pin_cnt = pin_stats + align_up(sizeof(SegStats) * nseg + 16, 64);
+    const size_t pin_rng = pin_cnt + 64;
+    const size_t pin_hist = align_up(pin_rng + sizeof(SeamRange) * (P.N / SEAM_CTA_MAX + 1), 64);
+    const size_t pin_need = pin_hist + sizeof(uint32_t) * 4 * RADIX_BINS + 256;
     if ((rc = ensure_pinned(w, pin_need, s))) return rc;
     size_t total = 0;
     Layout L = carve(w->arena, nseg, P.N, P.NB, kb, anypay, rows, &total);
@@ -754,29 +809,42 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     const int pblocks = (o.polish_blocks >= 1 && o.polish_blocks <= 3) ? o.polish_blocks : 3;
     sa.polish_cap = polish_capacity(kb, anypay, rows, P.wlog, pblocks, &sa.polish_smem);
     sa.allow_defer = 1;
+    sa.ranges = L.ranges;
+    sa.max_ranges = P.NB + (uint32_t)nseg;
+    sa.seam_cnt = L.seam_cnt;
+    sa.seam_suf = L.bmax;  // free once the polish has run
+    sa.seam_cut = reinterpret_cast<unsigned long long *>(L.carry);
     CK(launch_rounds(sa, s));
     CK(mark(4));
     CK(launch_finalize(sa, s));
     CK(mark(5));
     CK(launch_polish(sa, s));
     CK(mark(6));
-    CK(launch_seam_repair(sa, s));
+    CK(launch_seam_repair(sa, sm_count(), s));
     if (sa.allow_defer) {
-        // one wait at the end of the pipeline: large seam repairs run as multi-block sorts
-        unsigned char *hp0 = w->pinned + align_up(sizeof(Seg) * nseg, 64);
-        CK(cudaMemcpyAsync(hp0, L.stats, sizeof(SegStats) * nseg, cudaMemcpyDeviceToHost, s));
+        // one wait at the end of the pipeline: long seam ranges run as one multi-block sort
+        uint32_t *hc = reinterpret_cast<uint32_t *>(w->pinned + pin_cnt);
+        CK(cudaMemcpyAsync(hc, L.seam_cnt, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        for (int i = 0; i < nseg; ++i) {
-            SegStats d;
-            std::memcpy(&d, hp0 + sizeof(SegStats) * i, sizeof(SegStats));
-            if (d.repair_lo_hi_valid == 2)
-                if ((rc = global_repair(w, L, P.segs[i], d.repair_lo, d.repair_hi, kb, dtype, s))) return rc;
+        const uint32_t nlong = hc[1];
+        if (nlong) {
+            if (nlong > P.N / SEAM_CTA_MAX + 1) return NNSORT_E_STATE;
+            SeamRange *hr = reinterpret_cast<SeamRange *>(w->pinned + pin_rng);
+            CK(cudaMemcpyAsync(hr, L.ranges + (sa.max_ranges - nlong), sizeof(SeamRange) * nlong,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (uint32_t i = 0; i < nlong; ++i) {
+                const SeamRange r = hr[i];
+                if (r.seg >= (uint32_t)nseg || r.hi > P.segs[r.seg].n || r.lo >= r.hi) return NNSORT_E_STATE;
+            }
+            uint32_t *hh = reinterpret_cast<uint32_t *>(w->pinned + pin_hist);
+            if ((rc = repair_long_ranges(w, L, hr, nlong, nseg, kb, dtype, anypay, hh, s))) return rc;
         }
     }
     CK(mark(7));
 
     if (o.no_sync && !st) return NNSORT_OK;
-    unsigned char *hp = w->pinned + align_up(sizeof(Seg) * nseg, 64);
+    unsigned char *hp = w->pinned + pin_stats;
     CK(cudaMemcpyAsync(hp, L.stats, sizeof(SegStats) * nseg, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hp + sizeof(SegStats) * nseg, L.err, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -916,6 +984,7 @@ int nnsort_sort_host(void *h_keys, int32_t *h_payload, uint64_t n, int32_t dtype
 int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_model *f, float m,
                    int32_t precision, uint32_t *d_slots, float *d_y, cudaStream_t stream) {
     if (!f || !dtype_ok(dtype) || f->desc.dtype != dtype || !(m > 0.0f)) return NNSORT_E_INVALID_ARG;
+    if (precision < NNSORT_PREC_FP32 || precision > NNSORT_PREC_BF16X2) return NNSORT_E_INVALID_ARG;
     if (n && !d_keys) return NNSORT_E_INVALID_ARG;
     if (n >= 0xFFFFFFFFull || (double)n * m >= 4294967295.0) return NNSORT_E_INVALID_ARG;
     if (n == 0) return NNSORT_OK;

@@ -50,12 +50,11 @@ struct Seg {
 struct SegStats {
     unsigned long long count_ge[MAXR + 1];  // elements whose round index is >= r (r >= 1)
     unsigned long long ooo[MAXR];           // out-of-order inserts of o_r
-    unsigned long long repaired;
+    unsigned long long repaired;             // elements in the seam repair ranges
     unsigned int t;                          // completed iterations
     unsigned int oversized;
-    unsigned int repair_lo_hi_valid;
+    unsigned int ranges;                     // seam repair ranges
     unsigned int pad;
-    unsigned long long repair_lo, repair_hi;
 };
 
 // (order image, tie-break) pair; the maximum of an empty set is {0, 0, 0}

@@ -89,6 +89,12 @@ cudaError_t launch_bucket_bounds(const uint32_t *gs, uint64_t N, uint32_t nb, in
                                  uint32_t *bstart, cudaStream_t s);
 
 // ---- rounds / finalize / polish / seam / repair (k_solve.cu)
+// an output range [lo, hi) of array `seg` (positions relative to the array) to be re-sorted
+struct SeamRange {
+    unsigned long long lo, hi;
+    uint32_t seg, pad;
+};
+
 struct SolveArgs {
     const Seg *segs;
     int nseg;
@@ -115,13 +121,22 @@ struct SolveArgs {
     int key_bytes, dtype;
     int polish_cap;           // elements a bucket may hold on chip
     size_t polish_smem;
-    int allow_defer;          // 1: a large seam repair is left to the host's multi-block sort
+    int allow_defer;          // 1: seam repairs above SEAM_CTA_MAX are left to the host's
+                              //    multi-block sort (never when rows are carried)
+    SeamRange *ranges;        // [max_ranges]: block-sized repairs from the front, large from the back
+    uint32_t max_ranges;      // >= NB + nseg
+    uint32_t *seam_cnt;       // [4]: block-sized ranges, large ranges, next range to repair
+    OKey *seam_suf;           // [NB] scratch: smallest element of the later buckets
+    unsigned long long *seam_cut;  // [2 NB] scratch: first and last sorted-boundary cut per bucket
 };
 constexpr uint64_t SEAM_CTA_MAX = 1u << 16;  // largest seam repair one block performs
 cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s);
-cudaError_t launch_seam_repair(const SolveArgs &a, cudaStream_t s);
+cudaError_t launch_seam_repair(const SolveArgs &a, int sms, cudaStream_t s);
+cudaError_t launch_seam_pack(const SeamRange *rg, uint32_t nr, const Seg *segs, uint64_t total,
+                             int key_bytes, void *pk, uint32_t *pp, uint32_t *ps, int unpack, int sms,
+                             cudaStream_t s);
 int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks_per_sm,
                     size_t *smem_bytes);
 

@@ -102,11 +102,12 @@ static cudaError_t go(const PredictArgs &p, int sms, cudaStream_t s) {
     return nns_launched(cudaGetLastError());
 }
 
-cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, int sms, cudaStream_t s);
+cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, bool split, int sms, cudaStream_t s);
 
 cudaError_t launch_predict(const PadArch &a, int precision, const PredictArgs &p, int sms,
                            cudaStream_t s) {
-    if (precision == NNSORT_PREC_BF16 && a.layers == 2) return launch_predict_bf16(a, p, sms, s);
+    if ((precision == NNSORT_PREC_BF16 || precision == NNSORT_PREC_BF16X2) && a.layers == 2)
+        return launch_predict_bf16(a, p, precision == NNSORT_PREC_BF16X2, sms, s);
     if (a.layers == 1) {
         switch (a.h1) {
         case 8: return go<8, 0>(p, sms, s);

@@ -37,8 +37,6 @@ namespace nns {
 
 constexpr int SOLVE_THREADS = 512;
 constexpr int SNW = SOLVE_THREADS / 32;
-constexpr int ROUND_ITEMS = 16;
-constexpr int ROUND_CAP = SOLVE_THREADS * ROUND_ITEMS;  // 8192
 
 __device__ __forceinline__ int seg_of_bucket(const Seg *segs, int nseg, uint32_t b) {
     int lo = 0, hi = nseg - 1;
@@ -55,41 +53,24 @@ template <typename W> __device__ __forceinline__ W ldk(const void *p, size_t i) 
 
 __device__ __forceinline__ KMax kmax_none() { KMax r; r.k = 0; r.tb = 0; r.valid = 0; return r; }
 
-// block reduction of an array of MAXR maxima (one per iteration); result in out[] on all threads
-__device__ __forceinline__ void block_reduce_kmax_rounds(const KMax (&v)[MAXR], int eps,
-                                                         KMax *sm /*[SNW][MAXR]*/, KMax *out) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) {
-        if (r >= eps) break;
-        KMax x = v[r];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            KMax y;
-            y.k = __shfl_down_sync(0xFFFFFFFFu, x.k, o);
-            y.tb = __shfl_down_sync(0xFFFFFFFFu, x.tb, o);
-            y.valid = __shfl_down_sync(0xFFFFFFFFu, x.valid, o);
-            x = kmax(x, y);
-        }
-        if (lane == 0) sm[w * MAXR + r] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < (unsigned)eps) {
-        KMax x = kmax_none();
-        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) x = kmax(x, sm[ww * MAXR + threadIdx.x]);
-        out[threadIdx.x] = x;
-    }
-    __syncthreads();
+// ---------------------------------------------------------------------------------------------
+// k_rounds: one block per bucket. A bucket of up to rounds_cap(wlog) elements keeps its local
+// positions and round indices in shared memory next to the position table; larger buckets keep the
+// round indices in the global rank array.
+constexpr int RT = 256;  // threads of a rounds block
+__host__ __device__ constexpr uint32_t rounds_cap(int wlog) {
+    return wlog <= 12 ? (2u << wlog) : (1u << wlog);
+}
+__host__ __device__ constexpr size_t rounds_smem(int wlog) {
+    return ((size_t)4 << wlog) + (size_t)3 * rounds_cap(wlog);
 }
 
-// ---------------------------------------------------------------------------------------------
-// k_rounds
 template <typename W>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
-    extern __shared__ uint32_t tbl[];  // W positions
-    __shared__ KMax red[SNW * MAXR];
-    __shared__ KMax res[MAXR];
-    __shared__ unsigned int cge[MAXR + 1];
+__global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
+    extern __shared__ uint32_t tbl[];  // Wn claims | rcap local positions (u16) | rcap round indices (u8)
+    __shared__ KMax ks[33];
+    __shared__ KMax tot;
+    __shared__ unsigned int red_cnt[RT / 32];
     __shared__ int sh_seg;
     const int tid = threadIdx.x;
     const uint32_t b = blockIdx.x;
@@ -100,108 +81,71 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_rounds(SolveArgs a) {
         return;
     }
     if (tid == 0) sh_seg = seg_of_bucket(a.segs, a.nseg, b);
-    if (tid <= MAXR) cge[tid] = 0;
     __syncthreads();
-    const Seg &sg = a.segs[sh_seg];
-    const int eps = (int)sg.eps;
+    const int seg = sh_seg;
+    const int eps = (int)a.segs[seg].eps;
     const uint32_t Wn = 1u << a.wlog, wm = Wn - 1u;
+    const uint32_t rcap = rounds_cap(a.wlog);
     const int dt = a.dtype;
-    KMax mx[MAXR];
-    for (int r = 0; r < MAXR; ++r) mx[r] = kmax_none();
-    uint32_t ge[MAXR + 1];
-    for (int r = 0; r <= MAXR; ++r) ge[r] = 0;
-
-    if (nbk <= (uint32_t)ROUND_CAP) {
-        uint16_t ls[ROUND_ITEMS];
-        uint8_t cur[ROUND_ITEMS];
-        W okey[ROUND_ITEMS];  // loaded with the positions, used after the rounds
-#pragma unroll
-        for (int k = 0; k < ROUND_ITEMS; ++k) {
-            const uint32_t i = k * SOLVE_THREADS + tid;
-            cur[k] = 0;
-            ls[k] = (i < nbk) ? (uint16_t)(a.gs[s0 + i] & wm) : 0;
-            okey[k] = (i < nbk) ? ldk<W>(a.keys, s0 + i) : (W)0;
-        }
-        for (int r = 0; r < eps; ++r) {
-            for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) tbl[j] = EMPTY32;
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < ROUND_ITEMS; ++k) {
-                const uint32_t i = k * SOLVE_THREADS + tid;
-                if (i < nbk && cur[k] == r) atomicMin(&tbl[ls[k]], i);
-            }
-            __syncthreads();
-            int left = 0;
-#pragma unroll
-            for (int k = 0; k < ROUND_ITEMS; ++k) {
-                const uint32_t i = k * SOLVE_THREADS + tid;
-                if (i < nbk && cur[k] == r && tbl[ls[k]] != i) { cur[k] = (uint8_t)(r + 1); left = 1; }
-            }
-            if (__syncthreads_or(left) == 0) break;
-        }
-#pragma unroll
-        for (int k = 0; k < ROUND_ITEMS; ++k) {
-            const uint32_t i = k * SOLVE_THREADS + tid;
-            if (i < nbk) {
-                const int c = cur[k] > eps ? eps : cur[k];
-                a.rank[s0 + i] = (uint8_t)c;
-                KMax x;
-                x.k = ordbits(word64(okey[k]), dt);
-                x.tb = a.rows ? a.rows[s0 + i] : i;
-                x.valid = 1;
-                // compile-time round indices keep the per-round state in registers
-#pragma unroll
-                for (int r = 0; r < MAXR; ++r) {
-                    ge[r + 1] += (r + 1 <= eps && c >= r + 1) ? 1u : 0u;
-                    if (c == r && r < eps) mx[r] = kmax(mx[r], x);
-                }
-            }
-        }
-    } else {
-        // bucket beyond the register-resident capacity: state lives in the global rank array
-        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) a.rank[s0 + i] = 0;
+    const bool onchip = nbk <= rcap;
+    uint16_t *pos = reinterpret_cast<uint16_t *>(tbl + Wn);
+    uint8_t *cur = onchip ? reinterpret_cast<uint8_t *>(pos + rcap) : a.rank + s0;
+    for (uint32_t i = tid; i < nbk; i += RT) {
+        if (onchip) pos[i] = (uint16_t)(a.gs[s0 + i] & wm);
+        cur[i] = 0;
+    }
+    __syncthreads();
+    auto lpos = [&](uint32_t i) -> uint32_t { return onchip ? (uint32_t)pos[i] : (a.gs[s0 + i] & wm); };
+    // Algorithm NN-sort: in iteration r every element still unplaced claims its position; the
+    // lowest row (first arrival) is stored, the others move on to the next conflict array
+    const unsigned lanes_below = (1u << (tid & 31)) - 1u;
+    for (int r = 0; r < eps; ++r) {
+        for (uint32_t j = tid; j < Wn; j += RT) tbl[j] = EMPTY32;
         __syncthreads();
-        for (int r = 0; r < eps; ++r) {
-            for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) tbl[j] = EMPTY32;
-            __syncthreads();
-            for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS)
-                if (a.rank[s0 + i] == r) atomicMin(&tbl[a.gs[s0 + i] & wm], i);
-            __syncthreads();
-            int left = 0;
-            for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS)
-                if (a.rank[s0 + i] == r && tbl[a.gs[s0 + i] & wm] != i) {
-                    a.rank[s0 + i] = (uint8_t)(r + 1);
-                    left = 1;
-                }
-            if (__syncthreads_or(left) == 0) break;
+        // lanes of a warp hold consecutive rows: among lanes claiming the same position only the
+        // lowest can win, so only it issues the atomic (positions crowd when f is coarse)
+        for (uint32_t i0 = 0; i0 < nbk; i0 += RT) {
+            const uint32_t i = i0 + tid;
+            const bool act = i < nbk && cur[i] == r;
+            const uint32_t p = act ? lpos(i) : EMPTY32;
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, p);
+            if (act && (peers & lanes_below) == 0) atomicMin(&tbl[p], i);
         }
-        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) {
-            const int c = a.rank[s0 + i];
+        __syncthreads();
+        int left = 0;
+        for (uint32_t i = tid; i < nbk; i += RT)
+            if (cur[i] == r && tbl[lpos(i)] != i) { cur[i] = (uint8_t)(r + 1); left = 1; }
+        if (__syncthreads_or(left) == 0) break;
+    }
+    // per iteration: how many elements it stored and the largest of them (for the polish carry)
+    unsigned long long ge = nbk;  // elements whose round index is >= r
+    for (int r = 0; r < eps; ++r) {
+        KMax m = kmax_none();
+        unsigned int cnt = 0;
+        for (uint32_t i = tid; i < nbk; i += RT) {
+            if (cur[i] != r) continue;
             KMax x;
             x.k = ordbits(word64(ldk<W>(a.keys, s0 + i)), dt);
             x.tb = a.rows ? a.rows[s0 + i] : i;
             x.valid = 1;
-#pragma unroll
-            for (int r = 0; r < MAXR; ++r) {
-                ge[r + 1] += (r + 1 <= eps && c >= r + 1) ? 1u : 0u;
-                if (c == r && r < eps) mx[r] = kmax(mx[r], x);
-            }
+            m = kmax(m, x);
+            ++cnt;
         }
+        cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        if ((tid & 31) == 0) red_cnt[tid >> 5] = cnt;
+        block_excl_max(m, ks, &tot);  // ends with a barrier: red_cnt and tot are complete
+        if (tid == 0) {
+            unsigned int c = 0;
+            for (int w = 0; w < RT / 32; ++w) c += red_cnt[w];
+            ge -= c;
+            if (ge) atomicAdd(&a.stats[seg].count_ge[r + 1], ge);
+            OKey o; o.k = tot.k; o.tb = tot.tb; o.valid = tot.valid;
+            a.bmax[(size_t)b * MAXR + r] = o;
+        }
+        __syncthreads();
     }
-    // totals
-#pragma unroll
-    for (int r = 1; r <= MAXR; ++r) {
-        if (r > eps) break;
-        const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, ge[r]);
-        if ((tid & 31) == 0 && v) atomicAdd(&cge[r], v);
-    }
-    block_reduce_kmax_rounds(mx, eps, red, res);
-    if (tid >= 1 && tid <= eps && cge[tid]) atomicAdd(&a.stats[sh_seg].count_ge[tid], (unsigned long long)cge[tid]);
-    if (tid < eps) {
-        OKey o;
-        o.k = res[tid].k; o.tb = res[tid].tb; o.valid = res[tid].valid;
-        a.bmax[(size_t)b * MAXR + tid] = o;
-    }
+    if (onchip)
+        for (uint32_t i = tid; i < nbk; i += RT) a.rank[s0 + i] = cur[i];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -513,10 +457,16 @@ int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks
     const size_t fixed = sizeof(PolishSmem) + 256;
     const size_t tbl = ((size_t)4 << wlog);
     const size_t per = key_bytes + 2 + 1 + 1 + (payload ? 4 : 0) + (rows ? 4 : 0) + 3 * 2;
-    // shared memory per SM is 228 KB (227 KB usable by one block); each resident block reserves 1 KB
-    const size_t budget = (blocks_per_sm <= 1) ? 227 * 1024 : (228 * 1024) / blocks_per_sm - 1024 - 512;
-    long cap = (long)((budget - fixed - tbl) / per);
-    cap = std::min<long>(cap, 65534);
+    // shared memory per SM is 228 KB (227 KB usable by one block); each resident block reserves
+    // 1 KB. When the position table leaves no room at this many blocks per SM, fewer blocks share
+    // the SM; with no room even for one block every bucket takes the global-memory path.
+    long cap = 0;
+    for (int pb = std::max(1, blocks_per_sm); pb >= 1; --pb) {
+        const long budget = (pb == 1) ? 227L * 1024 : (228L * 1024) / pb - 1024 - 512;
+        cap = (budget - (long)fixed - (long)tbl - 64) / (long)per;
+        if (cap >= 256) break;
+    }
+    cap = std::max<long>(0, std::min<long>(cap, 65534));
     cap &= ~15L;
     if (smem_bytes) *smem_bytes = fixed + tbl + (size_t)cap * per + 64;
     return (int)cap;
@@ -602,103 +552,141 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// k_seam: one block per array. Locates elements that are smaller than some element of an
-// earlier bucket and re-sorts the smallest range of the output that contains them.
+// Seam repair. Every bucket's output is sorted; across buckets a non-monotone f can leave elements
+// on the wrong side of a bucket boundary. Call the boundary before output position p a cut; it is
+// sound when every element before it is <= every element after it (in (key, row) order when rows
+// are carried). The array is sorted exactly when every cut is sound, and sorting each maximal run
+// of elements between consecutive sound cuts, independently, sorts the array. Inside a bucket with
+// sorted elements e_0 <= ... <= e_{len-1}, preceded by elements whose maximum is P and followed by
+// elements whose minimum is S, the cut before e_j is sound iff P <= S and P <= e_j and
+// e_{j-1} <= S; with P <= S these hold for j in [#{e < P}, #{e <= S}], a non-empty interval.
+//   k_seam_scan  -- one block per array: per bucket the first and last sound cut, then the runs
+//                   between consecutive sound cuts that hold two or more elements.
+//   k_seam_fix   -- blocks take the runs of at most SEAM_CTA_MAX elements one by one and sort each
+//                   on chip; longer runs go to the multi-block sort on the host's side (or are
+//                   sorted here too when rows are carried or deferral is off).
+__device__ __forceinline__ KMax kinv(const KMax &x) {
+    KMax r; r.k = ~x.k; r.tb = ~x.tb; r.valid = x.valid; return r;
+}
+
 template <typename W>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_seam(SolveArgs a) {
-    extern __shared__ __align__(16) unsigned char sraw[];
-    PolishSmem &sm = *reinterpret_cast<PolishSmem *>(sraw);
+__global__ void __launch_bounds__(SOLVE_THREADS) k_seam_scan(SolveArgs a) {
     __shared__ KMax ks[33];
-    __shared__ unsigned long long sh_lo, sh_hi;
-    __shared__ KMax sh_minv;
-    __shared__ int sh_any;
+    __shared__ KMax tot;
     const int s = blockIdx.x, tid = threadIdx.x;
     if (*a.err) return;
     const Seg &sg = a.segs[s];
     const int dt = a.dtype;
     const W *outk = reinterpret_cast<const W *>(sg.keys);
     const uint32_t nb = sg.nb, bb = sg.bbase;
-    if (tid == 0) { sh_lo = ~0ull; sh_hi = 0; sh_any = 0; sh_minv.valid = 0; }
-    __syncthreads();
+    const unsigned long long n = sg.n, NONE = ~0ull;
     const uint32_t per = (nb + SOLVE_THREADS - 1) / SOLVE_THREADS;
-    const uint32_t c0 = std::min(nb, tid * per), c1 = std::min(nb, c0 + per);
+    // own chunk for forward passes, mirrored chunk for backward passes
+    const uint32_t c0 = min(nb, tid * per), c1 = min(nb, c0 + per);
+    const uint32_t mt = SOLVE_THREADS - 1 - tid;
+    const uint32_t m0 = min(nb, mt * per), m1 = min(nb, m0 + per);
+    auto bstart = [&](uint32_t bi) -> unsigned long long { return a.bstart[bi] - sg.ebase; };
     auto nonempty = [&](uint32_t bi) { return a.bstart[bi + 1] > a.bstart[bi]; };
     auto okey = [&](const OKey &o) { KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid; return x; };
+    auto elem = [&](unsigned long long pos, unsigned long long &k, uint32_t &tb) {
+        k = ordbits(word64(outk[pos]), dt);
+        tb = a.out_rows ? a.out_rows[sg.ebase + pos] : 0u;
+    };
+
+    // 1) S(b): the smallest element of the buckets after b (backward over the mirrored chunks)
     KMax loc = kmax_none();
+    for (uint32_t c = m0; c < m1; ++c)
+        if (nonempty(bb + c)) loc = kmax(loc, kinv(okey(a.blo[bb + c])));
+    KMax run = block_excl_max(loc, ks, nullptr);  // over the chunks after this one
+    for (uint32_t c = m1; c > m0; --c) {
+        const uint32_t bi = bb + c - 1;
+        if (!nonempty(bi)) continue;
+        const KMax sv = kinv(run);
+        OKey o; o.k = sv.k; o.tb = sv.tb; o.valid = sv.valid;
+        a.seam_suf[bi] = o;
+        run = kmax(run, kinv(okey(a.blo[bi])));
+    }
+    __syncthreads();
+
+    // 2) P(b): the largest element of the buckets before b; the bucket's sound cuts
+    loc = kmax_none();
     for (uint32_t c = c0; c < c1; ++c)
         if (nonempty(bb + c)) loc = kmax(loc, okey(a.bhi[bb + c]));
-    KMax run = block_excl_max(loc, ks, nullptr);
-    // element order of the output across buckets: by key, then by row when rows are carried
-    auto elem_less_pm = [&](uint64_t pos, const KMax &pm) {
-        const unsigned long long k = ordbits(word64(outk[pos]), dt);
-        const uint32_t tb = a.out_rows ? a.out_rows[sg.ebase + pos] : 0u;
-        return okey_less(k, tb, pm.k, pm.tb);
-    };
-    KMax minv = kmax_none();  // smallest violator (stored as a max with inverted meaning below)
-    unsigned long long hi = 0;
-    bool any = false;
+    run = block_excl_max(loc, ks, nullptr);
     for (uint32_t c = c0; c < c1; ++c) {
         const uint32_t bi = bb + c;
         if (!nonempty(bi)) continue;
-        const KMax lo = okey(a.blo[bi]);
-        if (run.valid && okey_less(lo.k, lo.tb, run.k, run.tb)) {
-            any = true;
-            // violators: the prefix of this bucket's sorted run below the running maximum
-            uint64_t l = a.bstart[bi] - sg.ebase, h = a.bstart[bi + 1] - sg.ebase;
-            while (l < h) {
-                const uint64_t mid = (l + h) >> 1;
-                if (elem_less_pm(mid, run)) l = mid + 1; else h = mid;
+        const KMax P = run, S = okey(a.seam_suf[bi]);
+        const unsigned long long b0 = bstart(bi), b1 = bstart(bi + 1);
+        unsigned long long fg = NONE, lg = NONE;
+        if (!(P.valid && S.valid && okey_less(S.k, S.tb, P.k, P.tb))) {
+            // A = #{e < P}
+            unsigned long long l = b0, h = b1;
+            if (P.valid) {
+                while (l < h) {
+                    const unsigned long long mid = (l + h) >> 1;
+                    unsigned long long k; uint32_t tb;
+                    elem(mid, k, tb);
+                    if (okey_less(k, tb, P.k, P.tb)) l = mid + 1; else h = mid;
+                }
             }
-            hi = std::max<unsigned long long>(hi, l);
-            if (!minv.valid || okey_less(lo.k, lo.tb, minv.k, minv.tb)) minv = lo;
+            fg = l;
+            // B = #{e <= S}
+            l = fg; h = b1;
+            if (S.valid) {
+                while (l < h) {
+                    const unsigned long long mid = (l + h) >> 1;
+                    unsigned long long k; uint32_t tb;
+                    elem(mid, k, tb);
+                    if (!okey_less(S.k, S.tb, k, tb)) l = mid + 1; else h = mid;
+                }
+            } else {
+                l = b1;
+            }
+            lg = l;
         }
+        a.seam_cut[2 * (size_t)bi] = fg;
+        a.seam_cut[2 * (size_t)bi + 1] = lg;
         run = kmax(run, okey(a.bhi[bi]));
     }
-    if (any) {
-        atomicOr(&sh_any, 1);
-        atomicMax(&sh_hi, hi);
-    }
     __syncthreads();
-    if (!sh_any) return;
-    // global minimum violator (serialised through thread 0 of each warp; rare path)
-    for (int w = 0; w < SOLVE_THREADS / 32; ++w) {
-        if ((tid >> 5) == w) {
-            for (int l = 0; l < 32; ++l) {
-                if ((tid & 31) == l && minv.valid &&
-                    (!sh_minv.valid || okey_less(minv.k, minv.tb, sh_minv.k, sh_minv.tb)))
-                    sh_minv = minv;
-                __syncwarp();
-            }
+
+    // 3) runs between consecutive sound cuts (backward: the next bucket's first sound cut)
+    auto emit = [&](unsigned long long lo, unsigned long long hi) {
+        if (hi - lo < 2) return;
+        atomicAdd(&a.stats[s].repaired, hi - lo);
+        atomicAdd(&a.stats[s].ranges, 1u);
+        SeamRange r; r.lo = lo; r.hi = hi; r.seg = (uint32_t)s; r.pad = 0;
+        if (a.allow_defer && !a.out_rows && hi - lo > SEAM_CTA_MAX) {
+            const uint32_t i = atomicAdd(&a.seam_cnt[1], 1u);
+            a.ranges[a.max_ranges - 1 - i] = r;
+        } else {
+            a.ranges[atomicAdd(&a.seam_cnt[0], 1u)] = r;
         }
-        __syncthreads();
+    };
+    loc = kmax_none();  // the smallest first sound cut of the chunk, as an inverted maximum
+    for (uint32_t c = m0; c < m1; ++c) {
+        const unsigned long long fg = nonempty(bb + c) ? a.seam_cut[2 * (size_t)(bb + c)] : NONE;
+        if (fg != NONE) { KMax x; x.k = ~fg; x.tb = 0; x.valid = 1; loc = kmax(loc, x); }
     }
-    if (tid == 0) {
-        // first output position holding an element greater than the smallest violator
-        const KMax mv = sh_minv;
-        uint32_t bs = bb;
-        for (uint32_t c = 0; c < nb; ++c) {
-            if (!nonempty(bb + c)) continue;
-            const KMax h = okey(a.bhi[bb + c]);
-            if (okey_less(mv.k, mv.tb, h.k, h.tb)) { bs = bb + c; break; }
-        }
-        uint64_t l = a.bstart[bs] - sg.ebase, h = a.bstart[bs + 1] - sg.ebase;
-        while (l < h) {
-            const uint64_t mid = (l + h) >> 1;
-            const unsigned long long k = ordbits(word64(outk[mid]), dt);
-            const uint32_t tb = a.out_rows ? a.out_rows[sg.ebase + mid] : 0u;
-            if (!okey_less(mv.k, mv.tb, k, tb)) l = mid + 1; else h = mid;
-        }
-        sh_lo = l;
-        const bool defer = a.allow_defer && !a.out_rows && (sh_hi - l) > SEAM_CTA_MAX;
-        a.stats[s].repair_lo = l;
-        a.stats[s].repair_hi = sh_hi;
-        a.stats[s].repair_lo_hi_valid = defer ? 2u : 1u;
-        a.stats[s].repaired = sh_hi - l;
+    run = block_excl_max(loc, ks, &tot);
+    unsigned long long nf = run.valid ? ~run.k : n;
+    for (uint32_t c = m1; c > m0; --c) {
+        const uint32_t bi = bb + c - 1;
+        if (!nonempty(bi)) continue;
+        const unsigned long long fg = a.seam_cut[2 * (size_t)bi], lg = a.seam_cut[2 * (size_t)bi + 1];
+        if (lg != NONE) emit(lg, nf);
+        if (fg != NONE) nf = fg;
     }
-    __syncthreads();
-    if (a.allow_defer && !a.out_rows && (sh_hi - sh_lo) > SEAM_CTA_MAX) return;
-    // re-sort [lo, hi) of the output by (key, row): the range is a union of sorted runs
-    const uint64_t lo = sh_lo, len = sh_hi - sh_lo;
+    if (tid == 0) emit(0, tot.valid ? ~tot.k : n);  // before the first sound cut
+}
+
+// re-sort out[lo, lo + len) of one array by (key, row): the range is a union of sorted runs
+template <typename W>
+__device__ void repair_range(const SolveArgs &a, PolishSmem &sm, const Seg &sg, uint64_t lo,
+                             uint32_t len) {
+    const int tid = threadIdx.x, dt = a.dtype;
+    W *outk = reinterpret_cast<W *>(sg.keys);
     uint32_t *X = a.g_x + sg.ebase + lo, *Y = a.g_y + sg.ebase + lo;
     for (uint32_t i = tid; i < len; i += SOLVE_THREADS) X[i] = i;
     __syncthreads();
@@ -707,17 +695,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam(SolveArgs a) {
     uint32_t *res = X;
     if (rr) {
         auto rkf = [&](uint32_t x) -> unsigned long long { return rr[x]; };
-        res = cta_radix_sort<uint32_t>(X, Y, (uint32_t)len, 32, rkf, sm.hist, sm.wcnt, sm.scratch);
+        res = cta_radix_sort<uint32_t>(X, Y, len, 32, rkf, sm.hist, sm.wcnt, sm.scratch);
     }
     uint32_t *oth = (res == X) ? Y : X;
     auto kkf = [&](uint32_t x) -> unsigned long long { return ordbits(word64(rk[x]), dt); };
-    res = cta_radix_sort<uint32_t>(res, oth, (uint32_t)len, a.key_bytes * 8, kkf, sm.hist, sm.wcnt,
-                                   sm.scratch);
+    res = cta_radix_sort<uint32_t>(res, oth, len, a.key_bytes * 8, kkf, sm.hist, sm.wcnt, sm.scratch);
     __syncthreads();
     // gather through scratch, then copy back
-    W *tk = reinterpret_cast<W *>(a.key_scratch) + sg.ebase;
-    uint32_t *tp = a.pay_scratch ? a.pay_scratch + sg.ebase : nullptr;
-    uint32_t *tr = a.row_scratch ? a.row_scratch + sg.ebase : nullptr;
+    W *tk = reinterpret_cast<W *>(a.key_scratch) + sg.ebase + lo;
+    uint32_t *tp = a.pay_scratch ? a.pay_scratch + sg.ebase + lo : nullptr;
+    uint32_t *tr = a.row_scratch ? a.row_scratch + sg.ebase + lo : nullptr;
     int32_t *op = sg.payload ? sg.payload + lo : nullptr;
     for (uint32_t i = tid; i < len; i += SOLVE_THREADS) {
         const uint32_t x = res[i];
@@ -726,20 +713,80 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam(SolveArgs a) {
         if (rr && tr) tr[i] = rr[x];
     }
     __syncthreads();
-    W *wk = reinterpret_cast<W *>(sg.keys) + lo;
     for (uint32_t i = tid; i < len; i += SOLVE_THREADS) {
-        wk[i] = tk[i];
+        outk[lo + i] = tk[i];
         if (op && tp) op[i] = (int32_t)tp[i];
         if (rr && tr) a.out_rows[sg.ebase + lo + i] = tr[i];
     }
+    __syncthreads();
+}
+
+template <typename W>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_seam_fix(SolveArgs a) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    PolishSmem &sm = *reinterpret_cast<PolishSmem *>(sraw);
+    __shared__ uint32_t sh_r;
+    if (*a.err) return;
+    const uint32_t nr = a.seam_cnt[0];
+    for (;;) {
+        if (threadIdx.x == 0) sh_r = atomicAdd(&a.seam_cnt[2], 1u);
+        __syncthreads();
+        const uint32_t r = sh_r;
+        __syncthreads();
+        if (r >= nr) break;
+        const SeamRange R = a.ranges[r];
+        repair_range<W>(a, sm, a.segs[R.seg], R.lo, (uint32_t)(R.hi - R.lo));
+    }
+}
+
+// Long seam ranges are sorted together: the cut between two ranges is sound, so every element of
+// one range is <= every element of the next, and one stable sort by key of all the ranges' elements,
+// packed in output order, leaves each range's elements (equal keys included) in its own stretch.
+// k_seam_pack copies the ranges (rg sorted by array and position, rg[j].pad = packed offset) into
+// the packed buffers or, with unpack = 1, back.
+template <typename W>
+__global__ void k_seam_pack(const SeamRange *rg, uint32_t nr, const Seg *segs, uint64_t total, W *pk,
+                            uint32_t *pp, uint32_t *ps, int unpack) {
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (rg[mid].pad <= q) lo = mid; else hi = mid - 1;
+        }
+        const SeamRange r = rg[lo];
+        const Seg &sg = segs[r.seg];
+        const uint64_t e = r.lo + (q - r.pad);
+        W *k = reinterpret_cast<W *>(sg.keys) + e;
+        if (!unpack) {
+            pk[q] = *k;
+            if (pp && sg.payload) pp[q] = (uint32_t)sg.payload[e];
+            if (ps) ps[q] = r.seg;
+        } else {
+            *k = pk[q];
+            if (pp && sg.payload) sg.payload[e] = (int32_t)pp[q];
+        }
+    }
+}
+
+cudaError_t launch_seam_pack(const SeamRange *rg, uint32_t nr, const Seg *segs, uint64_t total,
+                             int key_bytes, void *pk, uint32_t *pp, uint32_t *ps, int unpack, int sms,
+                             cudaStream_t s) {
+    if (total == 0 || nr == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)sms * 8);
+    if (key_bytes == 4)
+        k_seam_pack<uint32_t><<<grid, 256, 0, s>>>(rg, nr, segs, total, (uint32_t *)pk, pp, ps, unpack);
+    else
+        k_seam_pack<uint64_t><<<grid, 256, 0, s>>>(rg, nr, segs, total, (uint64_t *)pk, pp, ps, unpack);
+    return nns_launched(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------------------------
 template <typename W> static cudaError_t rounds_go(const SolveArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)4 << a.wlog;
+    const size_t smem = rounds_smem(a.wlog);
     cudaError_t e = cudaFuncSetAttribute(k_rounds<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_rounds<W><<<a.NB, SOLVE_THREADS, smem, s>>>(a);
+    k_rounds<W><<<a.NB, RT, smem, s>>>(a);
     return nns_launched(cudaGetLastError());
 }
 cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s) {
@@ -764,13 +811,16 @@ cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s) {
     return a.key_bytes == 4 ? polish_go<uint32_t>(a, s) : polish_go<uint64_t>(a, s);
 }
 
-template <typename W> static cudaError_t seam_go(const SolveArgs &a, cudaStream_t s) {
-    const size_t smem = sizeof(PolishSmem);
-    k_seam<W><<<a.nseg, SOLVE_THREADS, smem, s>>>(a);
+template <typename W> static cudaError_t seam_go(const SolveArgs &a, int sms, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.seam_cnt, 0, 4 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_seam_scan<W><<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
+    if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    k_seam_fix<W><<<2 * sms, SOLVE_THREADS, sizeof(PolishSmem), s>>>(a);
     return nns_launched(cudaGetLastError());
 }
-cudaError_t launch_seam_repair(const SolveArgs &a, cudaStream_t s) {
-    return a.key_bytes == 4 ? seam_go<uint32_t>(a, s) : seam_go<uint64_t>(a, s);
+cudaError_t launch_seam_repair(const SolveArgs &a, int sms, cudaStream_t s) {
+    return a.key_bytes == 4 ? seam_go<uint32_t>(a, sms, s) : seam_go<uint64_t>(a, sms, s);
 }
 
 }  // namespace nns

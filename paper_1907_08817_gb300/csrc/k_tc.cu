@@ -3,9 +3,11 @@
 //
 // Per tile of 128 keys (one key per thread, 4 warps):
 //   layer 1 (1 -> H)  binary32 FFMA, ReLU, rounded to BF16 and stored as the A operand
-//                     (128 x H, K-major, no swizzle: 8x8 core matrices of 128 bytes);
+//                     (128 x H, K-major, no swizzle: 8x8 core matrices of 128 bytes); with the
+//                     split form also the rounding residual, rounded to BF16, as a second A tile;
 //   layer 2 (H -> H)  tcgen05.mma.kind::f16, M = 128, N = H, K = H in steps of 16, issued by one
-//                     thread; B = W2 (H x H, K-major) staged once per block; D in TMEM;
+//                     thread; B = W2 (H x H, K-major) staged once per block; D in TMEM (the split
+//                     form accumulates A_hi W2^T + A_lo W2^T into the same D);
 //   epilogue          tcgen05.ld (thread t reads TMEM lane t = its key's row), + b2, ReLU, output
 //                     layer in binary32 FFMA, position rounding as in the binary32 path.
 // The MMA completion is signalled through an mbarrier whose wait gives up after a time limit
@@ -26,6 +28,7 @@ namespace {
 constexpr int TC_THREADS = 128;
 constexpr int TC_M = 128;
 constexpr size_t TC_SMEM = 32 * 1024;  // also caps residency at 7 blocks per SM (TMEM: 7 x 64 <= 512 columns)
+constexpr size_t TC_SMEM_SPLIT = 48 * 1024;  // second A tile; 4 blocks per SM
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -137,7 +140,7 @@ __device__ __forceinline__ int seg_of_tile_tc(const Seg *segs, int nseg, uint32_
 
 // Tiles here are 128 keys; the predict tile map (tbase, ntiles) is in units of PRED_TILE keys, so
 // a block walks PRED_TILE / 128 sub-tiles of each predict tile.
-template <int H, typename W>
+template <int H, typename W, bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     static_assert(H == 16 || H == 32 || H == 64, "tensor path widths");
     constexpr int NCOL = H < 32 ? 32 : H;
@@ -146,7 +149,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     constexpr uint32_t SBO_B = (H / 8) * 128;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sA = sm;                          // 128 x H bf16
-    unsigned char *sB = sA + TC_M * H * 2;           // H x H bf16
+    unsigned char *sA2 = sA + TC_M * H * 2;          // 128 x H bf16 residuals (split form)
+    unsigned char *sB = sA + (SPLIT ? 2 : 1) * TC_M * H * 2;  // H x H bf16
     float *sP = reinterpret_cast<float *>(sB + H * H * 2);  // W1 b1 b2 W3 b3
     __shared__ __align__(8) unsigned long long bar;
     __shared__ uint32_t tmem_base;
@@ -216,11 +220,16 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
 #pragma unroll
             for (int j0 = 0; j0 < H; j0 += 8) {
                 __align__(16) __nv_bfloat16 hb[8];
+                __align__(16) __nv_bfloat16 lb[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    hb[q] = __float2bfloat16_rn(relu_f(__fmaf_rn(sP[j0 + q], x, sP[H + j0 + q])));
+                for (int q = 0; q < 8; ++q) {
+                    const float h = relu_f(__fmaf_rn(sP[j0 + q], x, sP[H + j0 + q]));
+                    hb[q] = __float2bfloat16_rn(h);
+                    if (SPLIT) lb[q] = __float2bfloat16_rn(__fsub_rn(h, __bfloat162float(hb[q])));
+                }
                 const uint32_t off = (tid / 8) * SBO_A + (j0 / 8) * LBO + (tid % 8) * 16;
                 *reinterpret_cast<uint4 *>(sA + off) = *reinterpret_cast<const uint4 *>(hb);
+                if (SPLIT) *reinterpret_cast<uint4 *>(sA2 + off) = *reinterpret_cast<const uint4 *>(lb);
             }
             fence_async_smem();
             tc_fence_before();
@@ -232,6 +241,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                 for (int ks = 0; ks < H / 16; ++ks)
                     mma_bf16(tbase, mdesc(a0 + ks * 2 * LBO, LBO, SBO_A), mdesc(b0 + ks * 2 * LBO, LBO, SBO_B),
                              idesc, ks > 0 ? 1u : 0u);
+                if (SPLIT) {
+                    const uint32_t a1 = smem_u32(sA2);
+#pragma unroll
+                    for (int ks = 0; ks < H / 16; ++ks)
+                        mma_bf16(tbase, mdesc(a1 + ks * 2 * LBO, LBO, SBO_A),
+                                 mdesc(b0 + ks * 2 * LBO, LBO, SBO_B), idesc, 1u);
+                }
                 mma_commit(smem_u32(&bar));
             }
             if (!dead && !mbar_wait(smem_u32(&bar), phase)) {
@@ -294,27 +310,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
         if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
 }
 
-template <int H>
+template <int H, bool SPLIT>
 static cudaError_t bf16_go(const PredictArgs &p, int sms, cudaStream_t s) {
     const uint64_t subtiles = (uint64_t)p.total_tiles * (PRED_TILE / TC_M);
-    const int grid = (int)std::min<uint64_t>(subtiles, (uint64_t)sms * 7);
+    constexpr size_t smem = SPLIT ? TC_SMEM_SPLIT : TC_SMEM;
+    const int grid = (int)std::min<uint64_t>(subtiles, (uint64_t)sms * (SPLIT ? 4 : 7));
     if (grid == 0) return cudaSuccess;
-    auto k4 = k_predict_bf16<H, uint32_t>;
-    auto k8 = k_predict_bf16<H, uint64_t>;
+    auto k4 = k_predict_bf16<H, uint32_t, SPLIT>;
+    auto k8 = k_predict_bf16<H, uint64_t, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(p.key_bytes == 4 ? k4 : k8,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (p.key_bytes == 4) k4<<<grid, TC_THREADS, TC_SMEM, s>>>(p);
-    else k8<<<grid, TC_THREADS, TC_SMEM, s>>>(p);
+    if (p.key_bytes == 4) k4<<<grid, TC_THREADS, smem, s>>>(p);
+    else k8<<<grid, TC_THREADS, smem, s>>>(p);
     return nns_launched(cudaGetLastError());
 }
 
-cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, int sms, cudaStream_t s) {
+cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, bool split, int sms, cudaStream_t s) {
     if (a.layers != 2) return cudaErrorNotSupported;
     switch (a.h1) {
-    case 16: return bf16_go<16>(p, sms, s);
-    case 32: return bf16_go<32>(p, sms, s);
-    case 64: return bf16_go<64>(p, sms, s);
+    case 16: return split ? bf16_go<16, true>(p, sms, s) : bf16_go<16, false>(p, sms, s);
+    case 32: return split ? bf16_go<32, true>(p, sms, s) : bf16_go<32, false>(p, sms, s);
+    case 64: return split ? bf16_go<64, true>(p, sms, s) : bf16_go<64, false>(p, sms, s);
     }
     return cudaErrorNotSupported;  // widths below 16 stay on the binary32 path
 }

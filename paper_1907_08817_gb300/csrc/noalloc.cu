@@ -38,7 +38,8 @@ constexpr uint64_t NA_MAX_TILES = (NA_MAX_N + PART_TILE - 1) / PART_TILE;
 constexpr size_t NA_PER_ELEM = 2 * 4 + 2 * 8 + 2 * 4 + 1 + 1 + 3 * 4;  // gs, keys, payload, rank,
                                                                       // flag, three index lists
 constexpr size_t NA_BYTES = NA_MAX_N * NA_PER_ELEM + (size_t)NA_MAX_BUCKETS * (4 + 2 * MAXR * 16 + 32) +
-                            NA_MAX_TILES * RADIX_BINS * 8 + 2 * MAX_PASSES * RADIX_BINS * 4 + 64 * 1024;
+                            NA_MAX_TILES * RADIX_BINS * 8 + 2 * MAX_PASSES * RADIX_BINS * 4 +
+                            (size_t)(NA_MAX_BUCKETS + 1) * sizeof(SeamRange) + 64 * 1024;
 
 // the scratch: one per device that loads the library, held until the process exits
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
@@ -67,6 +68,7 @@ struct NaLayout {
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2];
     uint8_t *rank, *flag; uint32_t *gx, *gy, *gr, *bstart;
     OKey *bmax, *carry, *blo, *bhi;
+    SeamRange *ranges; uint32_t *seam_cnt;
     unsigned long long *lookback;
     size_t end;
 };
@@ -96,6 +98,8 @@ NaLayout na_carve(unsigned char *b) {
     L.carry = reinterpret_cast<OKey *>(take(sizeof(OKey) * NA_MAX_BUCKETS * MAXR));
     L.blo = reinterpret_cast<OKey *>(take(sizeof(OKey) * NA_MAX_BUCKETS));
     L.bhi = reinterpret_cast<OKey *>(take(sizeof(OKey) * NA_MAX_BUCKETS));
+    L.ranges = reinterpret_cast<SeamRange *>(take(sizeof(SeamRange) * (NA_MAX_BUCKETS + 1)));
+    L.seam_cnt = reinterpret_cast<uint32_t *>(take(16));
     L.lookback = reinterpret_cast<unsigned long long *>(take(8 * NA_MAX_TILES * RADIX_BINS));
     L.end = o;
     return L;
@@ -132,7 +136,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     if (n > NA_MAX_N) return NNSORT_E_INVALID_ARG;  // beyond the fixed scratch
     if (o.d_slots || o.d_fate) return NNSORT_E_INVALID_ARG;
     if (!(o.m > 0.0f) || o.eps < 0 || o.eps > NNSORT_MAX_ROUNDS) return NNSORT_E_INVALID_ARG;
-    if (o.precision != NNSORT_PREC_FP32 && o.precision != NNSORT_PREC_BF16) return NNSORT_E_INVALID_ARG;
+    if (o.precision < NNSORT_PREC_FP32 || o.precision > NNSORT_PREC_BF16X2) return NNSORT_E_INVALID_ARG;
     const int wlog = o.bucket_log2 ? o.bucket_log2 : 12;
     if (wlog < 9 || wlog > 14) return NNSORT_E_INVALID_ARG;
     if (st) std::memset(st, 0, sizeof(*st));
@@ -261,10 +265,15 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     sa.key_bytes = kb;
     sa.dtype = dtype;
     sa.polish_cap = polish_capacity(kb, pay, false, wlog, 2, &sa.polish_smem);
+    sa.ranges = L.ranges;
+    sa.max_ranges = sg.nb + 1;
+    sa.seam_cnt = L.seam_cnt;
+    sa.seam_suf = L.bmax;
+    sa.seam_cut = reinterpret_cast<unsigned long long *>(L.carry);
     NA_CK(launch_rounds(sa, s));
     NA_CK(launch_finalize(sa, s));
     NA_CK(launch_polish(sa, s));
-    NA_CK(launch_seam_repair(sa, s));
+    NA_CK(launch_seam_repair(sa, sms, s));
 
     // results: device statistics and the error word, read into host stack memory
     SegStats d;
@@ -290,6 +299,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
         st->buckets = sg.nb;
         st->oversized_buckets = d.oversized;
         st->repaired = d.repaired;
+        st->repair_ranges = d.ranges;
         st->partition_passes = (uint32_t)pp.npass;
         st->bucket_log2 = (uint32_t)wlog;
     }

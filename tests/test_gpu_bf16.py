@@ -27,13 +27,16 @@ def _bf16(a: np.ndarray) -> np.ndarray:
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def _emulate(params: np.ndarray, h: int, x: np.ndarray):
+def _emulate(params: np.ndarray, h: int, x: np.ndarray, split: bool = False):
     p = params.astype(np.float64)
     W2 = p[2 * h:2 * h + h * h].reshape(h, h)
     b2 = p[2 * h + h * h:3 * h + h * h]
     W3 = p[3 * h + h * h:4 * h + h * h]
     b3 = p[4 * h + h * h]
-    h1 = _bf16(orc.mlp_layer1_f32(2, h, h, params, x))  # binary32 first layer, then BF16
+    a = orc.mlp_layer1_f32(2, h, h, params, x)  # binary32 first layer
+    h1 = _bf16(a)
+    if split:  # the residual a - bf16(a) is exact in binary32, then rounded to BF16
+        h1 = h1 + _bf16((a.astype(np.float64) - h1).astype(np.float32))
     z = h1 @ _bf16(W2.astype(np.float32)).T
     h2 = np.maximum(z + b2, 0)
     terms = np.abs(h2 * W3).sum(axis=1) + abs(b3)
@@ -41,14 +44,15 @@ def _emulate(params: np.ndarray, h: int, x: np.ndarray):
 
 
 @pytest.mark.parametrize("h", [16, 32, 64])
-def test_bf16_forward_matches_emulation(h):
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+def test_bf16_forward_matches_emulation(h, prec):
     keys = W.lognormal_dup_f32(300_000, 31, sigma=2.0)
     om, _, _ = orc.train(keys, 2, h, h, orc.ORDBITS, sample_n=3000, steps=60, seed=h)
     f = lib_model(om)
     dk, _ = to_dev(keys)
-    slots, y = nns.predict(dk, f, precision="bf16")
+    slots, y = nns.predict(dk, f, precision=prec)
     x = orc.translate_f32(keys, om.norm)
-    ye, terms, zmag = _emulate(om.params, h, x)
+    ye, terms, zmag = _emulate(om.params, h, x, split=prec == "bf16x2")
     yg = y.cpu().numpy().astype(np.float64)
     W3 = np.abs(om.params[3 * h + h * h:4 * h + h * h].astype(np.float64))
     # tensor-core accumulation of z (<= 2 ulp of |z| terms) propagated through |W3|, plus the
@@ -59,19 +63,20 @@ def test_bf16_forward_matches_emulation(h):
     s32, _ = orc.predict_slots(keys, om)
     sg = slots.cpu().numpy().astype(np.int64)
     d = np.abs(sg - s32.astype(np.int64))
-    print(f"H={h}: |slot_bf16 - slot_fp32| mean {d.mean():.2f} max {d.max()}")
+    print(f"H={h} {prec}: |slot - slot_fp32| mean {d.mean():.2f} max {d.max()}")
 
 
 @pytest.mark.parametrize("h", [32, 64])
-def test_bf16_sort_matches_oracle_given_its_positions(h):
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+def test_bf16_sort_matches_oracle_given_its_positions(h, prec):
     keys = W.lognormal_dup_f32(400_000, 41, sigma=2.0)
     payload = np.arange(keys.shape[0], dtype=np.int32)
     om, _, _ = orc.train(keys, 2, h, h, orc.ORDBITS, sample_n=4000, steps=80, seed=h)
     f = lib_model(om)
     dk, _ = to_dev(keys)
-    slots, _ = nns.predict(dk, f, precision="bf16", want_y=False)
+    slots, _ = nns.predict(dk, f, precision=prec, want_y=False)
     dp = torch.from_numpy(payload).cuda()
-    st = nns.sort(dk, dp, f, precision="bf16")
+    st = nns.sort(dk, dp, f, precision=prec)
     L, _, _ = orc.nm_split(keys.shape[0])
     ok, op, ost, _ = orc.nnsort(keys, slots.cpu().numpy().astype(np.uint32), L, 3, 1024, payload)
     np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
@@ -92,3 +97,19 @@ def test_bf16_without_hidden_to_hidden_layer():
     with pytest.raises(nns.NNSortError) as ei:
         nns.sort(keys, None, tiny, precision="bf16")
     assert ei.value.status == -7
+
+
+def test_split_bf16_resolves_f_like_binary32():
+    """The split form carries ~16 significant bits of each activation: F(x) takes about as many
+    distinct values over the keys as the binary32 model, where plain BF16 collapses runs of
+    neighbouring keys onto one value."""
+    keys = np.sort(W.lognormal_f32(400_000, 51, sigma=2.0))
+    om, _, _ = orc.train(keys, 2, 64, 64, orc.ORDBITS, sample_n=4000, steps=80, seed=3)
+    f = lib_model(om)
+    dk, _ = to_dev(keys)
+    distinct = {}
+    for prec in ("fp32", "bf16", "bf16x2"):
+        _, y = nns.predict(dk, f, precision=prec)
+        distinct[prec] = int(torch.unique(y).numel())
+    assert distinct["bf16x2"] >= 0.9 * distinct["fp32"]
+    assert distinct["bf16x2"] > 2 * distinct["bf16"]

@@ -256,3 +256,122 @@ def test_host_entry_point():
     np.testing.assert_array_equal(bits(k2), bits(ok))
     np.testing.assert_array_equal(p2, op)
     assert stats_core(st) == stats_core(ost)
+
+
+# ---------------------------------------------------------------------------- tunables
+def test_every_bucket_width_and_polish_occupancy():
+    """Every (bucket_log2, polish_blocks) the autotuner may pick gives the oracle's output and
+    counts; at 2^14 positions per bucket the position table alone exceeds a third of an SM's shared
+    memory, so fewer polish blocks share the SM."""
+    keys = W.lognormal_dup_f32(200_003, 12, sigma=2.0)
+    om = _trained(keys, 1, 32, 0, orc.ORDBITS, S=2000, steps=60)
+    f = lib_model(om)
+    ok, _, ost, _ = orc.nnsort_model(keys, om)
+    for wlog in range(9, 15):
+        for pb in (1, 2, 3):
+            dk, kt = to_dev(keys)
+            st = nns.sort(dk, None, f, bucket_log2=wlog, polish_blocks=pb, key_type=kt)
+            np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+            assert stats_core(st) == stats_core(ost)
+            assert st["bucket_log2"] == wlog
+
+
+# ---------------------------------------------------------------------------- seam ranges
+def _expected_seam(keys: np.ndarray, slots: np.ndarray, wlog: int):
+    """From the definition: concatenate the buckets, each sorted by key; a cut between positions
+    p-1 and p is sound when max(out[:p]) <= min(out[p:]); the ranges to re-sort are the gaps of two
+    or more elements between consecutive sound cuts. Returns (count, elements)."""
+    n = keys.shape[0]
+    out = keys[np.lexsort((keys, slots.astype(np.int64) >> wlog))].astype(np.float64)
+    pm = np.maximum.accumulate(out)[:-1]           # max(out[:p]) for p = 1 .. n-1
+    sm = np.minimum.accumulate(out[::-1])[::-1][1:]  # min(out[p:]) for p = 1 .. n-1
+    cuts = np.concatenate(([0], 1 + np.nonzero(pm <= sm)[0], [n]))
+    gaps = np.diff(cuts)
+    big = gaps[gaps >= 2]
+    return int(big.shape[0]), int(big.sum())
+
+
+@pytest.mark.parametrize("n,moves,far", [(100_000, 0, False), (100_000, 40, False),
+                                         (1_000_000, 300, False), (1_000_000, 300, True)])
+def test_seam_repairs_exactly_the_unsound_ranges(n, moves, far):
+    """Positions that follow the key order except for a few keys sent a little (or, with far=True,
+    one key sent very far) across bucket boundaries: the repair touches exactly the ranges between
+    consecutive sound cuts; a range longer than one block handles runs as the multi-block sort."""
+    rs = np.random.RandomState(n + moves + far)
+    keys = W.uniform_f32(n, 21)
+    L, _, _ = orc.nm_split(n)
+    rank = np.argsort(np.argsort(keys, kind="stable"), kind="stable")
+    slots = (rank * 5 // 4).astype(np.int64)
+    idx = rs.choice(n, moves, replace=False)
+    slots[idx] += rs.randint(-6000, 6000, moves)
+    if far:
+        slots[np.argmin(keys)] = L - 1
+    slots = np.clip(slots, 0, L - 1).astype(np.uint32)
+    dk, kt = to_dev(keys)
+    ds = torch.from_numpy(slots.view(np.int32)).cuda()
+    st = nns.sort(dk, None, None, slots=ds, key_type=kt, bucket_log2=12)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(np.sort(keys, kind="stable")))
+    cnt, elems = _expected_seam(keys, slots, 12)
+    assert (st["repair_ranges"], st["repaired"]) == (cnt, elems)
+    if moves and not far:
+        assert cnt >= 2
+    if far:  # the smallest key in the last bucket: one range over nearly the whole array
+        assert cnt == 1 and elems > n - 4096
+
+
+def test_many_long_seam_ranges_sorted_together():
+    """Five stretches of the key order mapped to positions in reverse: five unsound ranges of
+    ~180K keys each (longer than one block repairs), separated by sound cuts, repaired by one packed
+    multi-block sort. With a payload (and a non-monotone model, so that no row trace is kept) the
+    payload follows its keys and equal keys keep input order."""
+    n = 2_000_000
+    rs = np.random.RandomState(77)
+    keys = np.round(W.uniform_f32(n, 22) * 1e5).astype(np.float32)  # many equal keys
+    L, _, _ = orc.nm_split(n)
+    rank = np.argsort(np.argsort(keys, kind="stable"), kind="stable")
+    slots = (rank * 5 // 4).astype(np.int64)
+    for c in rs.choice(np.arange(1, 9), 5, replace=False):
+        lo, hi = c * 200_000, c * 200_000 + 180_000
+        sel = (rank >= lo) & (rank < hi)
+        slots[sel] = (lo * 5 // 4) + ((hi - 1 - rank[sel]) * 5 // 4)
+    slots = np.clip(slots, 0, L - 1).astype(np.uint32)
+    dk, kt = to_dev(keys)
+    ds = torch.from_numpy(slots.view(np.int32)).cuda()
+    st = nns.sort(dk, None, None, slots=ds, key_type=kt, bucket_log2=12)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(np.sort(keys, kind="stable")))
+    cnt, elems = _expected_seam(keys, slots, 12)
+    assert (st["repair_ranges"], st["repaired"]) == (cnt, elems)
+    assert cnt >= 5 and elems > 5 * 65_536
+    # payload through the model path: an untrained two-layer model is non-monotone
+    keys = np.round(W.lognormal_f32(1_500_000, 23, sigma=1.0) * 1e3).astype(np.float32)
+    payload = np.arange(keys.shape[0], dtype=np.int32)
+    om = _rand_model(orc.F32, keys, 2, 16, 16, orc.ORDBITS, seed=9)
+    dk, _ = to_dev(keys)
+    dp = torch.from_numpy(payload).cuda()
+    st = nns.sort(dk, dp, lib_model(om))
+    ok, op, ost, _ = orc.nnsort_model(keys, om, payload=payload)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    np.testing.assert_array_equal(dp.cpu().numpy(), op)
+    assert stats_core(st) == stats_core(ost)
+    assert st["repaired"] > 65_536
+
+
+def test_batch_long_seams_stay_in_their_array():
+    """Arrays over the same key range, each with a non-monotone (untrained) model: every array has
+    seam ranges longer than one block repairs; they are sorted together by key and then by array,
+    so no key moves to another array. Payload rows follow their keys."""
+    arrs, oms, pays = [], [], []
+    for j in range(7):
+        a = W.uniform_f32(200_000 + 37_000 * j, 60 + j)
+        arrs.append(a)
+        oms.append(_rand_model(orc.F32, a, 2, 16, 16, orc.ORDBITS, seed=20 + j))
+        pays.append(np.arange(a.shape[0], dtype=np.int32))
+    dks = [to_dev(a)[0] for a in arrs]
+    dps = [torch.from_numpy(p.copy()).cuda() for p in pays]
+    sts = nns.sort_batch(dks, [lib_model(om) for om in oms], dps)
+    for a, om, p, dk, dp, st in zip(arrs, oms, pays, dks, dps, sts):
+        ok, op, ost, _ = orc.nnsort_model(a, om, payload=p)
+        np.testing.assert_array_equal(bits(from_dev(dk, a)), bits(ok))
+        np.testing.assert_array_equal(dp.cpu().numpy(), op)
+        assert stats_core(st) == stats_core(ost)
+    assert sum(st["repaired"] > 65_536 for st in sts) >= 2
