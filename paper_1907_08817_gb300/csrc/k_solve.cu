@@ -90,9 +90,22 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
     const bool onchip = nbk <= rcap;
     uint16_t *pos = reinterpret_cast<uint16_t *>(tbl + Wn);
     uint8_t *cur = onchip ? reinterpret_cast<uint8_t *>(pos + rcap) : a.rank + s0;
-    for (uint32_t i = tid; i < nbk; i += RT) {
-        if (onchip) pos[i] = (uint16_t)(a.gs[s0 + i] & wm);
-        cur[i] = 0;
+    constexpr int LB = 8;  // loads per thread issued together
+    for (uint32_t i0 = 0; i0 < nbk; i0 += RT * LB) {
+        uint32_t g[LB];
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const uint32_t i = i0 + q * RT + tid;
+            g[q] = (onchip && i < nbk) ? a.gs[s0 + i] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const uint32_t i = i0 + q * RT + tid;
+            if (i < nbk) {
+                if (onchip) pos[i] = (uint16_t)(g[q] & wm);
+                cur[i] = 0;
+            }
+        }
     }
     __syncthreads();
     auto lpos = [&](uint32_t i) -> uint32_t { return onchip ? (uint32_t)pos[i] : (a.gs[s0 + i] & wm); };
@@ -122,14 +135,26 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
     for (int r = 0; r < eps; ++r) {
         KMax m = kmax_none();
         unsigned int cnt = 0;
-        for (uint32_t i = tid; i < nbk; i += RT) {
-            if (cur[i] != r) continue;
-            KMax x;
-            x.k = ordbits(word64(ldk<W>(a.keys, s0 + i)), dt);
-            x.tb = a.rows ? a.rows[s0 + i] : i;
-            x.valid = 1;
-            m = kmax(m, x);
-            ++cnt;
+        for (uint32_t i0 = 0; i0 < nbk; i0 += RT * LB) {
+            W kv[LB];
+            bool hit[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = i0 + q * RT + tid;
+                hit[q] = i < nbk && cur[i] == r;
+                kv[q] = hit[q] ? ldk<W>(a.keys, s0 + i) : (W)0;
+            }
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                if (!hit[q]) continue;
+                const uint32_t i = i0 + q * RT + tid;
+                KMax x;
+                x.k = ordbits(word64(kv[q]), dt);
+                x.tb = a.rows ? a.rows[s0 + i] : i;
+                x.valid = 1;
+                m = kmax(m, x);
+                ++cnt;
+            }
         }
         cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
         if ((tid & 31) == 0) red_cnt[tid >> 5] = cnt;

@@ -1,7 +1,7 @@
 // k_tc.cu -- w_pos <- w.map(f) with the hidden-to-hidden layer of a two-hidden-layer f on the
 // fifth-generation tensor cores (tcgen05): BF16 operands, FP32 accumulation in tensor memory.
 //
-// Per tile of 128 keys (one key per thread, 4 warps):
+// Per sub-tile of KPT x 128 keys (KPT keys per thread, 4 warps):
 //   layer 1 (1 -> H)  binary32 FFMA, ReLU, rounded to BF16 and stored as the A operand
 //                     (128 x H, K-major, no swizzle: 8x8 core matrices of 128 bytes); with the
 //                     split form also the rounding residual, rounded to BF16, as a second A tile;
@@ -27,8 +27,6 @@ namespace {
 
 constexpr int TC_THREADS = 128;
 constexpr int TC_M = 128;
-constexpr size_t TC_SMEM = 32 * 1024;  // also caps residency at 7 blocks per SM (TMEM: 7 x 64 <= 512 columns)
-constexpr size_t TC_SMEM_SPLIT = 48 * 1024;  // second A tile; 4 blocks per SM
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -138,24 +136,37 @@ __device__ __forceinline__ int seg_of_tile_tc(const Seg *segs, int nseg, uint32_
 
 }  // namespace
 
-// Tiles here are 128 keys; the predict tile map (tbase, ntiles) is in units of PRED_TILE keys, so
-// a block walks PRED_TILE / 128 sub-tiles of each predict tile.
-template <int H, typename W, bool SPLIT>
+// A block of 128 threads walks sub-tiles of KPT * 128 keys (thread t handles keys t, t + 128, ...);
+// the predict tile map (tbase, ntiles) is in units of PRED_TILE keys. Key group g of a sub-tile has
+// its own A tile(s) and its own accumulator (TMEM columns [g H, (g+1) H)), so every parameter
+// loaded from shared memory serves KPT keys. Parameters are read as float4 (broadcast).
+__host__ __device__ constexpr int tc_ncol(int H, int KPT) {
+    return KPT * H <= 32 ? 32 : (KPT * H <= 64 ? 64 : (KPT * H <= 128 ? 128 : 256));
+}
+template <int H, bool SPLIT, int KPT>
+__host__ __device__ constexpr size_t tc_smem_bytes(int npass) {
+    return (size_t)KPT * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)H * H * 2 + (size_t)(4 * H + 4) * 4 +
+           (size_t)npass * RADIX_BINS * 4;
+}
+
+template <int H, typename W, bool SPLIT, int KPT>
 __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     static_assert(H == 16 || H == 32 || H == 64, "tensor path widths");
-    constexpr int NCOL = H < 32 ? 32 : H;
+    static_assert(PRED_TILE % (KPT * TC_M) == 0, "sub-tiles tile the predict tile");
+    constexpr int NT = SPLIT ? 2 : 1;          // A tiles per key group: hi (and lo)
+    constexpr uint32_t TILE_B = TC_M * H * 2;  // bytes of one 128 x H BF16 tile
+    constexpr int NCOL = tc_ncol(H, KPT);
     constexpr uint32_t LBO = 128;              // next core matrix along K
-    constexpr uint32_t SBO_A = (H / 8) * 128;  // next 8-row group
-    constexpr uint32_t SBO_B = (H / 8) * 128;
+    constexpr uint32_t SBO = (H / 8) * 128;    // next 8-row group
+    constexpr int SUB = KPT * TC_M;
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *sA = sm;                          // 128 x H bf16
-    unsigned char *sA2 = sA + TC_M * H * 2;          // 128 x H bf16 residuals (split form)
-    unsigned char *sB = sA + (SPLIT ? 2 : 1) * TC_M * H * 2;  // H x H bf16
-    float *sP = reinterpret_cast<float *>(sB + H * H * 2);  // W1 b1 b2 W3 b3
+    unsigned char *sB = sm + KPT * NT * TILE_B;                       // H x H bf16
+    float *pf = reinterpret_cast<float *>(sB + H * H * 2);            // W1 | b1 | b2 | W3 | b3
+    const float4 *pv = reinterpret_cast<const float4 *>(pf);
+    uint32_t *sh_hist = reinterpret_cast<uint32_t *>(pf + 4 * H + 4);
     __shared__ __align__(8) unsigned long long bar;
     __shared__ uint32_t tmem_base;
     __shared__ int sh_seg;
-    __shared__ uint32_t sh_hist[MAX_PASSES * RADIX_BINS];
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int npass = a.hist ? a.plan.npass : 0;
@@ -175,8 +186,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     bool dead = false;  // set once a wait gave up: no further MMAs are issued
     uint32_t dead_parity = 0;
     int loaded = -1;
-    const uint32_t sub_per_tile = PRED_TILE / TC_M;
+    const uint32_t sub_per_tile = PRED_TILE / SUB;
     const uint64_t total = (uint64_t)a.total_tiles * sub_per_tile;
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    const uint32_t aoff = (tid / 8) * SBO + (tid % 8) * 16;  // this thread's row in an A tile
 
     for (uint64_t st = blockIdx.x; st < total; st += gridDim.x) {
         const uint32_t tile = (uint32_t)(st / sub_per_tile), sub = (uint32_t)(st % sub_per_tile);
@@ -186,67 +199,92 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
         const int si = sh_seg;
         const Seg &sg = a.segs[si];
         const uint64_t n = sg.n;
-        const uint64_t i = (uint64_t)(tile - sg.tbase) * PRED_TILE + (uint64_t)sub * TC_M + tid;
-        if ((uint64_t)(tile - sg.tbase) * PRED_TILE + (uint64_t)sub * TC_M >= n) continue;  // whole sub-tile past the end
+        const uint64_t r0 = (uint64_t)(tile - sg.tbase) * PRED_TILE + (uint64_t)sub * SUB;
+        if (r0 >= n) continue;  // whole sub-tile past the end of its array
         const bool model = sg.slots == nullptr;
         if (model && si != loaded) {
             // W2 (row k = output unit, K = input unit j) -> bf16 canonical K-major layout
             const float *W2 = sg.params + 2 * H;
             for (int e = tid; e < H * H; e += TC_THREADS) {
                 const int nrow = e / H, k = e % H;
-                const uint32_t off = (nrow / 8) * SBO_B + (k / 8) * LBO + (nrow % 8) * 16 + (k % 8) * 2;
+                const uint32_t off = (nrow / 8) * SBO + (k / 8) * LBO + (nrow % 8) * 16 + (k % 8) * 2;
                 *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16_rn(W2[e]);
             }
             for (int e = tid; e < H; e += TC_THREADS) {
-                sP[e] = sg.params[e];                          // W1
-                sP[H + e] = sg.params[H + e];                  // b1
-                sP[2 * H + e] = sg.params[2 * H + H * H + e];  // b2
-                sP[3 * H + e] = sg.params[3 * H + H * H + e];  // W3
+                pf[e] = sg.params[e];                          // W1
+                pf[H + e] = sg.params[H + e];                  // b1
+                pf[2 * H + e] = sg.params[2 * H + H * H + e];  // b2
+                pf[3 * H + e] = sg.params[3 * H + H * H + e];  // W3
             }
-            if (tid == 0) sP[4 * H] = sg.params[4 * H + H * H];  // b3
+            if (tid == 0) pf[4 * H] = sg.params[4 * H + H * H];  // b3
             loaded = si;
             fence_async_smem();
             __syncthreads();
         }
-        const bool valid = i < n;
         const W *keys = reinterpret_cast<const W *>(sg.keys);
-        const uint64_t w = valid ? word64(keys[i]) : 0ull;
-        if (valid && key_is_nan(w, a.dtype)) err |= ERR_NAN;
-        float y = 0.0f;
-        uint32_t slot = 0;
+        uint64_t wv[KPT];
+        bool valid[KPT];
+#pragma unroll
+        for (int g = 0; g < KPT; ++g) {
+            const uint64_t i = r0 + (uint64_t)g * TC_M + tid;
+            valid[g] = i < n;
+            wv[g] = valid[g] ? word64(keys[i]) : 0ull;
+            if (valid[g] && key_is_nan(wv[g], a.dtype)) err |= ERR_NAN;
+        }
+        float y[KPT];
+        uint32_t slot[KPT];
+#pragma unroll
+        for (int g = 0; g < KPT; ++g) { y[g] = 0.0f; slot[g] = 0; }
         if (model) {
-            const float x = valid ? translate_x(w, sg.norm) : 0.0f;
-            // layer 1 -> A row `tid`
+            float x[KPT];
+#pragma unroll
+            for (int g = 0; g < KPT; ++g) x[g] = valid[g] ? translate_x(wv[g], sg.norm) : 0.0f;
+            // layer 1 -> row `tid` of key group g's A tile(s)
 #pragma unroll
             for (int j0 = 0; j0 < H; j0 += 8) {
-                __align__(16) __nv_bfloat16 hb[8];
-                __align__(16) __nv_bfloat16 lb[8];
+                const float4 wa = pv[j0 / 4], wb = pv[j0 / 4 + 1];
+                const float4 ba = pv[H / 4 + j0 / 4], bb = pv[H / 4 + j0 / 4 + 1];
+                const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float h = relu_f(__fmaf_rn(sP[j0 + q], x, sP[H + j0 + q]));
-                    hb[q] = __float2bfloat16_rn(h);
-                    if (SPLIT) lb[q] = __float2bfloat16_rn(__fsub_rn(h, __bfloat162float(hb[q])));
+                for (int g = 0; g < KPT; ++g) {
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float h0 = relu_f(__fmaf_rn(w8[2 * q], x[g], b8[2 * q]));
+                        const float h1 = relu_f(__fmaf_rn(w8[2 * q + 1], x[g], b8[2 * q + 1]));
+                        const __nv_bfloat162 p = __floats2bfloat162_rn(h0, h1);
+                        hi[q] = *reinterpret_cast<const uint32_t *>(&p);
+                        if (SPLIT) {
+                            const float2 f = __bfloat1622float2(p);
+                            const __nv_bfloat162 r = __floats2bfloat162_rn(__fsub_rn(h0, f.x), __fsub_rn(h1, f.y));
+                            lo[q] = *reinterpret_cast<const uint32_t *>(&r);
+                        }
+                    }
+                    unsigned char *t0 = sm + (g * NT) * TILE_B + aoff + (j0 / 8) * LBO;
+                    *reinterpret_cast<uint4 *>(t0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    if (SPLIT) *reinterpret_cast<uint4 *>(t0 + TILE_B) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                 }
-                const uint32_t off = (tid / 8) * SBO_A + (j0 / 8) * LBO + (tid % 8) * 16;
-                *reinterpret_cast<uint4 *>(sA + off) = *reinterpret_cast<const uint4 *>(hb);
-                if (SPLIT) *reinterpret_cast<uint4 *>(sA2 + off) = *reinterpret_cast<const uint4 *>(lb);
             }
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
             if (tid == 0 && !dead) {
-                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+                const uint32_t b0 = smem_u32(sB);
 #pragma unroll
-                for (int ks = 0; ks < H / 16; ++ks)
-                    mma_bf16(tbase, mdesc(a0 + ks * 2 * LBO, LBO, SBO_A), mdesc(b0 + ks * 2 * LBO, LBO, SBO_B),
-                             idesc, ks > 0 ? 1u : 0u);
-                if (SPLIT) {
-                    const uint32_t a1 = smem_u32(sA2);
+                for (int g = 0; g < KPT; ++g) {
+                    const uint32_t a0 = smem_u32(sm + (g * NT) * TILE_B);
 #pragma unroll
                     for (int ks = 0; ks < H / 16; ++ks)
-                        mma_bf16(tbase, mdesc(a1 + ks * 2 * LBO, LBO, SBO_A),
-                                 mdesc(b0 + ks * 2 * LBO, LBO, SBO_B), idesc, 1u);
+                        mma_bf16(tbase + g * H, mdesc(a0 + ks * 2 * LBO, LBO, SBO),
+                                 mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc, ks > 0 ? 1u : 0u);
+                    if (SPLIT) {
+#pragma unroll
+                        for (int ks = 0; ks < H / 16; ++ks)
+                            mma_bf16(tbase + g * H, mdesc(a0 + TILE_B + ks * 2 * LBO, LBO, SBO),
+                                     mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc, 1u);
+                    }
                 }
                 mma_commit(smem_u32(&bar));
             }
@@ -258,42 +296,63 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
             phase ^= 1u;
             dead = __syncthreads_or(dead);
             tc_fence_after();
-            float acc[16];
-            float yy = sP[4 * H];
-            const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+            float yy[KPT];
+#pragma unroll
+            for (int g = 0; g < KPT; ++g) yy[g] = pf[4 * H];
 #pragma unroll
             for (int c0 = 0; c0 < H; c0 += 16) {
-                if (!dead) {
-                    tmem_ld16(lane_addr + c0, acc);
-                    tmem_wait_ld();
-                } else {
+                float b2[16], w3[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+                for (int v = 0; v < 4; ++v) {
+                    const float4 bq = pv[2 * H / 4 + c0 / 4 + v], wq = pv[3 * H / 4 + c0 / 4 + v];
+                    b2[4 * v] = bq.x; b2[4 * v + 1] = bq.y; b2[4 * v + 2] = bq.z; b2[4 * v + 3] = bq.w;
+                    w3[4 * v] = wq.x; w3[4 * v + 1] = wq.y; w3[4 * v + 2] = wq.z; w3[4 * v + 3] = wq.w;
                 }
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    yy = __fmaf_rn(sP[3 * H + c0 + q], relu_f(__fadd_rn(acc[q], sP[2 * H + c0 + q])), yy);
+                for (int g = 0; g < KPT; ++g) {
+                    float acc[16];
+                    if (!dead) {
+                        tmem_ld16(lane_addr + g * H + c0, acc);
+                        tmem_wait_ld();
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        yy[g] = __fmaf_rn(w3[q], relu_f(__fadd_rn(acc[q], b2[q])), yy[g]);
+                }
             }
-            y = yy;
-            slot = slot_of(y, sg.nm_hi, sg.nm_lo, sg.L);
+#pragma unroll
+            for (int g = 0; g < KPT; ++g) {
+                y[g] = yy[g];
+                slot[g] = slot_of(yy[g], sg.nm_hi, sg.nm_lo, sg.L);
+            }
             tc_fence_before();
-        } else if (valid) {
-            slot = sg.slots[i];
-            if ((uint64_t)slot >= sg.L) { err |= ERR_SLOT; slot = 0; }
+        } else {
+#pragma unroll
+            for (int g = 0; g < KPT; ++g) {
+                if (!valid[g]) continue;
+                slot[g] = sg.slots[r0 + (uint64_t)g * TC_M + tid];
+                if ((uint64_t)slot[g] >= sg.L) { err |= ERR_SLOT; slot[g] = 0; }
+            }
         }
-        if (valid) {
+#pragma unroll
+        for (int g = 0; g < KPT; ++g) {
+            if (!valid[g]) continue;
+            const uint64_t i = r0 + (uint64_t)g * TC_M + tid;
             const uint64_t e = sg.ebase + i;
-            const uint32_t g = (uint32_t)(sg.gs_base + slot);
-            if (a.gs) a.gs[e] = g;
-            if (a.key_copy) reinterpret_cast<W *>(a.key_copy)[e] = (W)w;
+            const uint32_t gpos = (uint32_t)(sg.gs_base + slot[g]);
+            if (a.gs) a.gs[e] = gpos;
+            if (a.key_copy) reinterpret_cast<W *>(a.key_copy)[e] = (W)wv[g];
             if (a.pay_copy && sg.payload) a.pay_copy[e] = (uint32_t)sg.payload[i];
             if (a.row_init) a.row_init[e] = (uint32_t)i;
-            if (a.slots_out) a.slots_out[e] = slot;
-            if (a.y_out) a.y_out[e] = y;
+            if (a.slots_out) a.slots_out[e] = slot[g];
+            if (a.y_out) a.y_out[e] = y[g];
 #pragma unroll
             for (int p = 0; p < MAX_PASSES; ++p) {
                 if (p >= npass) break;
-                const uint32_t d = (g >> a.plan.shift[p]) & ((1u << a.plan.bits[p]) - 1u);
+                const uint32_t d = (gpos >> a.plan.shift[p]) & ((1u << a.plan.bits[p]) - 1u);
                 atomicAdd(&sh_hist[p * RADIX_BINS + d], 1u);
             }
         }
@@ -310,14 +369,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
         if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
 }
 
-template <int H, bool SPLIT>
+template <int H, bool SPLIT, int KPT>
 static cudaError_t bf16_go(const PredictArgs &p, int sms, cudaStream_t s) {
-    const uint64_t subtiles = (uint64_t)p.total_tiles * (PRED_TILE / TC_M);
-    constexpr size_t smem = SPLIT ? TC_SMEM_SPLIT : TC_SMEM;
-    const int grid = (int)std::min<uint64_t>(subtiles, (uint64_t)sms * (SPLIT ? 4 : 7));
+    const uint64_t subtiles = (uint64_t)p.total_tiles * (PRED_TILE / (KPT * TC_M));
+    const int npass = p.hist ? p.plan.npass : 0;
+    // resident blocks per SM: bounded by tensor memory (512 columns) and by shared memory (228 KB,
+    // 1 KB reserved per block); the request is raised so that shared memory never admits more
+    // blocks than tensor memory can serve (a block waiting in tcgen05.alloc would hold its slot)
+    constexpr int NCOL = tc_ncol(H, KPT);
+    const int by_tmem = std::min(512 / NCOL, 2048 / TC_THREADS);
+    size_t smem = tc_smem_bytes<H, SPLIT, KPT>(npass);
+    const size_t floor_req = (size_t)(228 * 1024) / (size_t)(by_tmem + 1) - 1024 + 64;
+    smem = std::max(smem, floor_req);
+    const int by_smem = (int)((size_t)(228 * 1024) / (smem + 1024));
+    const int per_sm = std::max(1, std::min(by_tmem, by_smem));
+    const int grid = (int)std::min<uint64_t>(subtiles, (uint64_t)sms * per_sm);
     if (grid == 0) return cudaSuccess;
-    auto k4 = k_predict_bf16<H, uint32_t, SPLIT>;
-    auto k8 = k_predict_bf16<H, uint64_t, SPLIT>;
+    auto k4 = k_predict_bf16<H, uint32_t, SPLIT, KPT>;
+    auto k8 = k_predict_bf16<H, uint64_t, SPLIT, KPT>;
     cudaError_t e = cudaFuncSetAttribute(p.key_bytes == 4 ? k4 : k8,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -326,12 +395,14 @@ static cudaError_t bf16_go(const PredictArgs &p, int sms, cudaStream_t s) {
     return nns_launched(cudaGetLastError());
 }
 
+constexpr int TC_KPT = 2;  // keys per thread per sub-tile
+
 cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, bool split, int sms, cudaStream_t s) {
     if (a.layers != 2) return cudaErrorNotSupported;
     switch (a.h1) {
-    case 16: return split ? bf16_go<16, true>(p, sms, s) : bf16_go<16, false>(p, sms, s);
-    case 32: return split ? bf16_go<32, true>(p, sms, s) : bf16_go<32, false>(p, sms, s);
-    case 64: return split ? bf16_go<64, true>(p, sms, s) : bf16_go<64, false>(p, sms, s);
+    case 16: return split ? bf16_go<16, true, TC_KPT>(p, sms, s) : bf16_go<16, false, TC_KPT>(p, sms, s);
+    case 32: return split ? bf16_go<32, true, TC_KPT>(p, sms, s) : bf16_go<32, false, TC_KPT>(p, sms, s);
+    case 64: return split ? bf16_go<64, true, TC_KPT>(p, sms, s) : bf16_go<64, false, TC_KPT>(p, sms, s);
     }
     return cudaErrorNotSupported;  // widths below 16 stay on the binary32 path
 }
