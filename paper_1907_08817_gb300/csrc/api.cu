@@ -439,6 +439,8 @@ struct Layout {
     uint8_t *rank; uint8_t *g_flag; uint32_t *g_x, *g_y, *g_r; uint32_t *bstart;
     OKey *bmax, *carry, *blo, *bhi;
     SeamRange *ranges; uint32_t *seam_cnt;
+    uint32_t *order, *order_cnt;
+    BigRange *big; uint32_t *big_cnt;
 };
 
 Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, bool pay, bool rows,
@@ -471,6 +473,10 @@ Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, boo
     L.bhi = c.take<OKey>(NB);
     L.ranges = c.take<SeamRange>((size_t)NB + nseg);
     L.seam_cnt = c.take<uint32_t>(4);
+    L.order = c.take<uint32_t>(NB);
+    L.order_cnt = c.take<uint32_t>(4);
+    L.big = c.take<BigRange>(N / POLISH_BIG + 1);
+    L.big_cnt = c.take<uint32_t>(4);
     *total = align_up(c.off, 256);
     return L;
 }
@@ -576,42 +582,30 @@ void fill_stats(const Seg &s, const SegStats &d, nnsort_stats *st) {
     st->repair_ranges = d.ranges;
 }
 
-// the long seam ranges hr[0..nr) (host copy), sorted together: packed in output order into the
-// (now free) partition buffers key[0] / pay[0], stable multi-block radix sort by key, then (when
-// the ranges belong to more than one array) by array index, unpacked. `hp` is pinned staging for
-// the array-index histograms.
-int repair_long_ranges(Workspace *w, Layout &L, SeamRange *hr, uint32_t nr, int nseg, int kb,
-                       int dtype, bool anypay, uint32_t *hp, cudaStream_t s) {
-    std::sort(hr, hr + nr, [](const SeamRange &x, const SeamRange &y) {
-        return x.seg != y.seg ? x.seg < y.seg : x.lo < y.lo;
-    });
-    uint64_t total = 0;
-    for (uint32_t j = 0; j < nr; ++j) {
-        hr[j].pad = (uint32_t)total;
-        total += hr[j].hi - hr[j].lo;
-    }
-    if (total < 2) return NNSORT_OK;
-    const bool multi = hr[0].seg != hr[nr - 1].seg;
-    CK(cudaMemcpyAsync(L.ranges, hr, sizeof(SeamRange) * nr, cudaMemcpyHostToDevice, s));
-    uint32_t *pay0 = anypay ? L.pay[0] : nullptr;
-    const int sms = sm_count();
-    CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, L.key[0], pay0, multi ? L.gs[0] : nullptr,
-                        0, sms, s));
+// Stable multi-block radix sort of `total` packed elements: by key (every 8-bit digit of the order
+// image), then, when `gmax` > 0, stably by a group index in [0, gmax] carried alongside (J). K, P, J
+// are ping-pong pairs with the data in index 0 (P nullable, J null when gmax == 0); `glen` lists
+// (group, elements) for the group passes' histograms, staged through the pinned `hp`
+// (4 x RADIX_BINS words). *fin receives the index of the pair holding the result.
+int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void *const K[2],
+                uint32_t *const P[2], uint32_t *const J[2], uint32_t gmax,
+                const std::vector<std::pair<uint32_t, uint64_t>> &glen, uint32_t *hp, int *fin,
+                cudaStream_t s) {
     auto pass = [&](int p, int si, bool keydig, int shift, int bits, const uint32_t *base) -> int {
         const int di = si ^ 1;
         OnesweepArgs a{};
         a.N = total;
-        a.key_in = L.key[si];
-        a.key_out = L.key[di];
-        if (pay0) {
-            a.pay_in = L.pay[si];
-            a.pay_out = L.pay[di];
+        a.key_in = K[si];
+        a.key_out = K[di];
+        if (P[0]) {
+            a.pay_in = P[si];
+            a.pay_out = P[di];
         }
         if (keydig) {
-            if (multi) { a.row_in = L.gs[si]; a.row_out = L.gs[di]; }
+            if (gmax) { a.row_in = J[si]; a.row_out = J[di]; }
         } else {
-            a.gs_in = L.gs[si];
-            a.gs_out = L.gs[di];
+            a.gs_in = J[si];
+            a.gs_out = J[di];
         }
         a.key_digits = keydig ? 1 : 0;
         a.shift = shift;
@@ -627,39 +621,96 @@ int repair_long_ranges(Workspace *w, Layout &L, SeamRange *hr, uint32_t nr, int 
         return NNSORT_OK;
     };
     int rc;
-    const int npass = kb;  // 8-bit digits of the key's order image; even, so the result ends in key[0]
+    const int npass = kb;  // even, so the key passes end in pair 0
     CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
     CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
-    CK(launch_key_hist(L.key[0], total, kb, dtype, npass, L.hist, s));
+    CK(launch_key_hist(K[0], total, kb, dtype, npass, L.hist, s));
     CK(launch_digit_bases(L.hist, L.bases, npass, s));
     for (int p = 0; p < npass; ++p)
         if ((rc = pass(p, p & 1, true, 8 * p, 8, L.bases + p * RADIX_BINS))) return rc;
-    int fin = 0;
-    if (multi) {
-        // array-index passes of at most 9 bits; their histograms come from the ranges' lengths
-        int sbits = 1;
-        while ((1u << sbits) < (uint32_t)nseg) ++sbits;
-        const int nsp = (sbits + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
+    *fin = 0;
+    if (gmax) {
+        // group-index passes of at most 9 bits
+        int gbits = 1;
+        while ((1ull << gbits) <= (unsigned long long)gmax) ++gbits;
+        const int nsp = (gbits + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
+        if (nsp > 4) return NNSORT_E_INVALID_ARG;
         std::memset(hp, 0, sizeof(uint32_t) * 4 * RADIX_BINS);
         int sh[4], bt[4];
         for (int q = 0, at = 0; q < nsp; ++q) {
-            bt[q] = (sbits - at + (nsp - q) - 1) / (nsp - q);
+            bt[q] = (gbits - at + (nsp - q) - 1) / (nsp - q);
             sh[q] = at;
             at += bt[q];
-            for (uint32_t j = 0; j < nr; ++j)
-                hp[q * RADIX_BINS + ((hr[j].seg >> sh[q]) & ((1u << bt[q]) - 1u))] +=
-                    (uint32_t)(hr[j].hi - hr[j].lo);
+            for (const auto &gl : glen)
+                hp[q * RADIX_BINS + ((gl.first >> sh[q]) & ((1u << bt[q]) - 1u))] += (uint32_t)gl.second;
         }
         CK(cudaMemcpyAsync(L.hist, hp, sizeof(uint32_t) * nsp * RADIX_BINS, cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
         CK(launch_digit_bases(L.hist, L.bases, nsp, s));
         for (int q = 0; q < nsp; ++q)
             if ((rc = pass(q, q & 1, false, sh[q], bt[q], L.bases + q * RADIX_BINS))) return rc;
-        fin = nsp & 1;
+        *fin = nsp & 1;
     }
-    CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, L.key[fin], anypay ? L.pay[fin] : nullptr,
-                        nullptr, 1, sms, s));
+    return NNSORT_OK;
+}
+
+// the long seam ranges hr[0..nr) (host copy), sorted together: packed in output order into the
+// (now free) partition buffers key[0] / pay[0], stable multi-block radix sort by key, then (when
+// the ranges belong to more than one array) by array index, unpacked
+int repair_long_ranges(Workspace *w, Layout &L, SeamRange *hr, uint32_t nr, int kb, int dtype,
+                       bool anypay, uint32_t *hp, cudaStream_t s) {
+    std::sort(hr, hr + nr, [](const SeamRange &x, const SeamRange &y) {
+        return x.seg != y.seg ? x.seg < y.seg : x.lo < y.lo;
+    });
+    uint64_t total = 0;
+    std::vector<std::pair<uint32_t, uint64_t>> glen;
+    for (uint32_t j = 0; j < nr; ++j) {
+        hr[j].pad = (uint32_t)total;
+        total += hr[j].hi - hr[j].lo;
+        glen.emplace_back(hr[j].seg, hr[j].hi - hr[j].lo);
+    }
+    if (total < 2) return NNSORT_OK;
+    const bool multi = hr[0].seg != hr[nr - 1].seg;
+    CK(cudaMemcpyAsync(L.ranges, hr, sizeof(SeamRange) * nr, cudaMemcpyHostToDevice, s));
+    const int sms = sm_count();
+    void *const K[2] = {L.key[0], L.key[1]};
+    uint32_t *const P[2] = {anypay ? L.pay[0] : nullptr, anypay ? L.pay[1] : nullptr};
+    uint32_t *const J[2] = {L.gs[0], L.gs[1]};
+    CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, K[0], P[0], multi ? J[0] : nullptr, 0, sms, s));
+    int fin = 0, rc;
+    if ((rc = sort_packed(w, L, total, kb, dtype, K, P, J, multi ? hr[nr - 1].seg : 0u, glen, hp, &fin, s)))
+        return rc;
+    CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, K[fin], P[fin], nullptr, 1, sms, s));
     return NNSORT_OK;  // the next call on this stream waits before it rewrites the staging area
+}
+
+// buckets too large for one block's polish (listed by k_polish, host copy hb[0..nb)): their
+// elements, packed from the partition buffers (pair `src`), sorted by key and then by bucket, and
+// written to their output positions; then their first/last elements for the seam
+int sort_big_buckets(Workspace *w, Layout &L, BigRange *hb, uint32_t nb, int src, int kb, int dtype,
+                     bool anypay, uint32_t *hp, cudaStream_t s) {
+    std::sort(hb, hb + nb, [](const BigRange &x, const BigRange &y) { return x.lo < y.lo; });
+    uint64_t total = 0;
+    std::vector<std::pair<uint32_t, uint64_t>> glen;
+    for (uint32_t j = 0; j < nb; ++j) {
+        hb[j].off = (uint32_t)total;
+        total += hb[j].hi - hb[j].lo;
+        glen.emplace_back(j, hb[j].hi - hb[j].lo);
+    }
+    CK(cudaMemcpyAsync(L.big, hb, sizeof(BigRange) * nb, cudaMemcpyHostToDevice, s));
+    const int sms = sm_count(), o = src ^ 1;
+    // pack into the free pair, then ping-pong between it and the (now dead) source pair
+    void *const K[2] = {L.key[o], L.key[src]};
+    uint32_t *const P[2] = {anypay ? L.pay[o] : nullptr, anypay ? L.pay[src] : nullptr};
+    uint32_t *const J[2] = {L.gs[o], L.gs[src]};
+    CK(launch_big_pack(L.big, nb, L.segs, total, kb, L.key[src], anypay ? L.pay[src] : nullptr, K[0], P[0],
+                       nb > 1 ? J[0] : nullptr, 0, sms, s));
+    int fin = 0, rc;
+    if ((rc = sort_packed(w, L, total, kb, dtype, K, P, J, nb > 1 ? nb - 1 : 0u, glen, hp, &fin, s)))
+        return rc;
+    CK(launch_big_pack(L.big, nb, L.segs, total, kb, nullptr, nullptr, K[fin], P[fin], nullptr, 1, sms, s));
+    CK(launch_big_bounds(L.big, nb, L.segs, kb, dtype, L.blo, L.bhi, s));
+    return NNSORT_OK;
 }
 
 int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype, nnsort_stats *st,
@@ -704,7 +755,8 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     const size_t pin_cnt = pin_stats + align_up(sizeof(SegStats) * nseg + 16, 64);
     const size_t pin_rng = pin_cnt + 64;
     const size_t pin_hist = align_up(pin_rng + sizeof(SeamRange) * (P.N / SEAM_CTA_MAX + 1), 64);
-    const size_t pin_need = pin_hist + sizeof(uint32_t) * 4 * RADIX_BINS + 256;
+    const size_t pin_big = align_up(pin_hist + sizeof(uint32_t) * 4 * RADIX_BINS, 64);
+    const size_t pin_need = pin_big + sizeof(BigRange) * (P.N / POLISH_BIG + 1) + 256;
     if ((rc = ensure_pinned(w, pin_need, s))) return rc;
     size_t total = 0;
     Layout L = carve(w->arena, nseg, P.N, P.NB, kb, anypay, rows, &total);
@@ -814,11 +866,35 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     sa.seam_cnt = L.seam_cnt;
     sa.seam_suf = L.bmax;  // free once the polish has run
     sa.seam_cut = reinterpret_cast<unsigned long long *>(L.carry);
+    CK(launch_bucket_order(L.bstart, P.NB, (uint32_t)sa.polish_cap, L.order, L.order_cnt, s));
+    sa.order = L.order;
+    if (!rows) {
+        sa.big = L.big;
+        sa.big_cnt = L.big_cnt;
+        CK(cudaMemsetAsync(L.big_cnt, 0, sizeof(uint32_t), s));
+    }
     CK(launch_rounds(sa, s));
     CK(mark(4));
     CK(launch_finalize(sa, s));
     CK(mark(5));
     CK(launch_polish(sa, s));
+    if (sa.big) {
+        // buckets too large for one block: one wait, then one multi-block sort of all of them
+        uint32_t *hc = reinterpret_cast<uint32_t *>(w->pinned + pin_cnt);
+        CK(cudaMemcpyAsync(hc, L.big_cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const uint32_t nbig = hc[0];
+        if (nbig) {
+            if (nbig > P.N / POLISH_BIG + 1) return NNSORT_E_STATE;
+            BigRange *hb = reinterpret_cast<BigRange *>(w->pinned + pin_big);
+            CK(cudaMemcpyAsync(hb, L.big, sizeof(BigRange) * nbig, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (uint32_t j = 0; j < nbig; ++j)
+                if (hb[j].seg >= (uint32_t)nseg || hb[j].lo >= hb[j].hi || hb[j].hi > P.N) return NNSORT_E_STATE;
+            uint32_t *hh = reinterpret_cast<uint32_t *>(w->pinned + pin_hist);
+            if ((rc = sort_big_buckets(w, L, hb, nbig, fi, kb, dtype, anypay, hh, s))) return rc;
+        }
+    }
     CK(mark(6));
     CK(launch_seam_repair(sa, sm_count(), s));
     if (sa.allow_defer) {
@@ -838,7 +914,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
                 if (r.seg >= (uint32_t)nseg || r.hi > P.segs[r.seg].n || r.lo >= r.hi) return NNSORT_E_STATE;
             }
             uint32_t *hh = reinterpret_cast<uint32_t *>(w->pinned + pin_hist);
-            if ((rc = repair_long_ranges(w, L, hr, nlong, nseg, kb, dtype, anypay, hh, s))) return rc;
+            if ((rc = repair_long_ranges(w, L, hr, nlong, kb, dtype, anypay, hh, s))) return rc;
         }
     }
     CK(mark(7));

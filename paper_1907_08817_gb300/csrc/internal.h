@@ -95,6 +95,14 @@ struct SeamRange {
     uint32_t seg, pad;
 };
 
+// a bucket too large for one block's polish: partitioned elements [lo, hi) of array `seg`, bucket b,
+// offset `off` in the packed buffer
+struct BigRange {
+    unsigned long long lo, hi;
+    uint32_t seg, off, b, pad;
+};
+constexpr uint32_t POLISH_BIG = 1u << 16;  // buckets above this many elements sort multi-block
+
 struct SolveArgs {
     const Seg *segs;
     int nseg;
@@ -128,12 +136,23 @@ struct SolveArgs {
     uint32_t *seam_cnt;       // [4]: block-sized ranges, large ranges, next range to repair
     OKey *seam_suf;           // [NB] scratch: smallest element of the later buckets
     unsigned long long *seam_cut;  // [2 NB] scratch: first and last sorted-boundary cut per bucket
+    const uint32_t *order;    // [NB] nullable: block i of k_rounds / k_polish takes bucket order[i]
+    BigRange *big;            // nullable: k_polish lists buckets above POLISH_BIG here (and only
+    uint32_t *big_cnt;        //   splits their runs); their sort is left to the host's multi-block sort
 };
 constexpr uint64_t SEAM_CTA_MAX = 1u << 16;  // largest seam repair one block performs
+// order[]: buckets holding more than `heavy` elements first (they run longest), the rest after
+cudaError_t launch_bucket_order(const uint32_t *bstart, uint32_t NB, uint32_t heavy, uint32_t *order,
+                                uint32_t *cnt /*[2], zeroed here*/, cudaStream_t s);
 cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_seam_repair(const SolveArgs &a, int sms, cudaStream_t s);
+cudaError_t launch_big_pack(const BigRange *br, uint32_t nr, const Seg *segs, uint64_t total, int key_bytes,
+                            const void *src_k, const uint32_t *src_p, void *pk, uint32_t *pp, uint32_t *pj,
+                            int unpack, int sms, cudaStream_t s);
+cudaError_t launch_big_bounds(const BigRange *br, uint32_t nr, const Seg *segs, int key_bytes, int dtype,
+                              OKey *blo, OKey *bhi, cudaStream_t s);
 cudaError_t launch_seam_pack(const SeamRange *rg, uint32_t nr, const Seg *segs, uint64_t total,
                              int key_bytes, void *pk, uint32_t *pp, uint32_t *ps, int unpack, int sms,
                              cudaStream_t s);

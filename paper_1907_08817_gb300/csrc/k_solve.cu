@@ -54,6 +54,27 @@ template <typename W> __device__ __forceinline__ W ldk(const void *p, size_t i) 
 __device__ __forceinline__ KMax kmax_none() { KMax r; r.k = 0; r.tb = 0; r.valid = 0; return r; }
 
 // ---------------------------------------------------------------------------------------------
+// Bucket order for the per-bucket kernels: blocks are dispatched roughly in index order, so heavy
+// buckets listed first start first and run alongside the many light ones instead of forming a
+// tail. Heavy buckets fill order[] from the front, light ones from the back.
+__global__ void k_bucket_order(const uint32_t *bstart, uint32_t NB, uint32_t heavy, uint32_t *order,
+                               uint32_t *cnt) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= NB) return;
+    if (bstart[b + 1] - bstart[b] > heavy) order[atomicAdd(&cnt[0], 1u)] = b;
+    else order[NB - 1 - atomicAdd(&cnt[1], 1u)] = b;
+}
+
+cudaError_t launch_bucket_order(const uint32_t *bstart, uint32_t NB, uint32_t heavy, uint32_t *order,
+                                uint32_t *cnt, cudaStream_t s) {
+    if (NB == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_bucket_order<<<(NB + 255) / 256, 256, 0, s>>>(bstart, NB, heavy, order, cnt);
+    return nns_launched(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------------
 // k_rounds: one block per bucket. A bucket of up to rounds_cap(wlog) elements keeps its local
 // positions and round indices in shared memory next to the position table; larger buckets keep the
 // round indices in the global rank array.
@@ -73,7 +94,7 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
     __shared__ unsigned int red_cnt[RT / 32];
     __shared__ int sh_seg;
     const int tid = threadIdx.x;
-    const uint32_t b = blockIdx.x;
+    const uint32_t b = a.order ? a.order[blockIdx.x] : blockIdx.x;
     const uint32_t s0 = a.bstart[b], s1 = a.bstart[b + 1];
     const uint32_t nbk = s1 - s0;
     if (nbk == 0) {
@@ -116,18 +137,37 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
         for (uint32_t j = tid; j < Wn; j += RT) tbl[j] = EMPTY32;
         __syncthreads();
         // lanes of a warp hold consecutive rows: among lanes claiming the same position only the
-        // lowest can win, so only it issues the atomic (positions crowd when f is coarse)
-        for (uint32_t i0 = 0; i0 < nbk; i0 += RT) {
-            const uint32_t i = i0 + tid;
-            const bool act = i < nbk && cur[i] == r;
-            const uint32_t p = act ? lpos(i) : EMPTY32;
-            const unsigned peers = __match_any_sync(0xFFFFFFFFu, p);
-            if (act && (peers & lanes_below) == 0) atomicMin(&tbl[p], i);
+        // lowest can win, so only it issues the atomic (positions crowd when f is coarse). Loads are
+        // issued LB at a time (the round index and position may live in global memory).
+        for (uint32_t i0 = 0; i0 < nbk; i0 += RT * LB) {
+            uint32_t pv[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = i0 + q * RT + tid;
+                pv[q] = (i < nbk && cur[i] == r) ? lpos(i) : EMPTY32;
+            }
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = i0 + q * RT + tid;
+                const unsigned peers = __match_any_sync(0xFFFFFFFFu, pv[q]);
+                if (pv[q] != EMPTY32 && (peers & lanes_below) == 0) atomicMin(&tbl[pv[q]], i);
+            }
         }
         __syncthreads();
         int left = 0;
-        for (uint32_t i = tid; i < nbk; i += RT)
-            if (cur[i] == r && tbl[lpos(i)] != i) { cur[i] = (uint8_t)(r + 1); left = 1; }
+        for (uint32_t i0 = 0; i0 < nbk; i0 += RT * LB) {
+            uint32_t pv[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = i0 + q * RT + tid;
+                pv[q] = (i < nbk && cur[i] == r) ? lpos(i) : EMPTY32;
+            }
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = i0 + q * RT + tid;
+                if (pv[q] != EMPTY32 && tbl[pv[q]] != i) { cur[i] = (uint8_t)(r + 1); left = 1; }
+            }
+        }
         if (__syncthreads_or(left) == 0) break;
     }
     // per iteration: how many elements it stored and the largest of them (for the polish carry)
@@ -354,15 +394,31 @@ struct BucketView {
     }
 };
 
+// Fig. "Algorithm polish", first part: for each o_r its stored elements in position order, the
+// out-of-order split against the running maximum (carry from earlier buckets first) and the
+// in-order run R_r (appended to v.RL, offsets in sm.rl_off). Sets v.F for leftover elements (last
+// conflict array and out-of-order ones) and counts the out-of-order ones in sm.ooo.
 template <typename W, typename Idx>
-__device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx> &v,
-                              uint32_t b, uint32_t s0, uint32_t nbk, const Seg &sg) {
+__device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx> &v,
+                            uint32_t b, uint32_t nbk) {
     const int tid = threadIdx.x;
     const int t = sm.t;
     const uint32_t Wn = v.wm + 1u;
     const Idx EMPTY = (Idx)~(Idx)0;
-    const int keybits = (a.key_bytes == 4) ? 32 : 64;
-    for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.F[i] = (v.R[i] >= t) ? 1 : 0;
+    constexpr int LB = 8;  // element loads issued together (the view may be in global memory)
+    for (uint32_t i0 = 0; i0 < nbk; i0 += SOLVE_THREADS * LB) {
+        uint8_t rv[LB];
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const uint32_t i = i0 + q * SOLVE_THREADS + tid;
+            rv[q] = i < nbk ? v.R[i] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const uint32_t i = i0 + q * SOLVE_THREADS + tid;
+            if (i < nbk) v.F[i] = (rv[q] >= t) ? 1 : 0;
+        }
+    }
     if (tid <= MAXR) sm.rl_off[tid] = 0;
     if (tid < MAXR) sm.ooo[tid] = 0;
     if (tid < t) {
@@ -377,8 +433,17 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
         // o_r: stored elements in position order
         for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) v.TB[j] = EMPTY;
         __syncthreads();
-        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS)
-            if (v.R[i] == r) v.TB[v.ls(i)] = (Idx)i;
+        for (uint32_t i0 = 0; i0 < nbk; i0 += SOLVE_THREADS * LB) {
+            uint32_t pv[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const uint32_t i = i0 + q * SOLVE_THREADS + tid;
+                pv[q] = (i < nbk && v.R[i] == r) ? v.ls(i) : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int q = 0; q < LB; ++q)
+                if (pv[q] != 0xFFFFFFFFu) v.TB[pv[q]] = (Idx)(i0 + q * SOLVE_THREADS + tid);
+        }
         __syncthreads();
         const uint32_t per_s = (Wn + SOLVE_THREADS - 1) / SOLVE_THREADS;
         const uint32_t p0 = std::min(Wn, tid * per_s), p1 = std::min(Wn, p0 + per_s);
@@ -426,6 +491,15 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
         if (tid == 0) sm.rl_off[r + 1] = rl_n;
         __syncthreads();
     }
+}
+
+template <typename W, typename Idx>
+__device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx> &v,
+                              uint32_t b, uint32_t s0, uint32_t nbk, const Seg &sg) {
+    const int tid = threadIdx.x;
+    const int t = sm.t;
+    const int keybits = (a.key_bytes == 4) ? 32 : 64;
+    polish_runs<W, Idx>(a, sm, v, b, nbk);
     // leftover: the last conflict array and every out-of-order element, in input order
     const uint32_t per_e = (nbk + SOLVE_THREADS - 1) / SOLVE_THREADS;
     const uint32_t e0 = std::min(nbk, tid * per_e), e1 = std::min(nbk, e0 + per_e);
@@ -480,7 +554,7 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
 int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks_per_sm,
                     size_t *smem_bytes) {
     const size_t fixed = sizeof(PolishSmem) + 256;
-    const size_t tbl = ((size_t)4 << wlog);
+    const size_t tbl = ((size_t)2 << wlog);  // on chip the position table holds 16-bit indices
     const size_t per = key_bytes + 2 + 1 + 1 + (payload ? 4 : 0) + (rows ? 4 : 0) + 3 * 2;
     // shared memory per SM is 228 KB (227 KB usable by one block); each resident block reserves
     // 1 KB. When the position table leaves no room at this many blocks per SM, fewer blocks share
@@ -503,7 +577,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
     PolishSmem &sm = *reinterpret_cast<PolishSmem *>(praw);
     unsigned char *dyn = praw + ((sizeof(PolishSmem) + 15) & ~(size_t)15);
     const int tid = threadIdx.x;
-    const uint32_t b = blockIdx.x;
+    const uint32_t b = a.order ? a.order[blockIdx.x] : blockIdx.x;
     const uint32_t s0 = a.bstart[b], s1 = a.bstart[b + 1];
     const uint32_t nbk = s1 - s0;
     if (nbk == 0) return;
@@ -516,10 +590,28 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
     const Seg &sg = a.segs[sm.seg];
     const uint32_t Wn = 1u << a.wlog;
     const uint32_t cap = (uint32_t)a.polish_cap;
+    if (a.big && nbk > POLISH_BIG) {
+        // the runs of o_1..o_t are split here (out-of-order counts); the bucket's output -- the
+        // merge of the sorted leftover with the runs, i.e. its elements in (key, row) order -- is
+        // left to the multi-block sort of all such buckets
+        if (tid == 0) atomicAdd(&a.stats[sm.seg].oversized, 1u);
+        uint32_t *TB = reinterpret_cast<uint32_t *>(dyn);
+        BucketView<W, uint32_t> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
+                                  a.rank + s0, a.g_flag + s0, nullptr, nullptr, a.g_x + s0, a.g_y + s0,
+                                  a.g_r + s0, TB, Wn - 1u, a.dtype};
+        polish_runs<W, uint32_t>(a, sm, v, b, nbk);
+        if (tid < sm.t && sm.ooo[tid]) atomicAdd(&a.stats[sm.seg].ooo[tid], (unsigned long long)sm.ooo[tid]);
+        if (tid == 0) {
+            BigRange r;
+            r.lo = s0; r.hi = s1; r.seg = (uint32_t)sm.seg; r.off = 0; r.b = b; r.pad = 0;
+            a.big[atomicAdd(a.big_cnt, 1u)] = r;
+        }
+        return;
+    }
     if (nbk <= cap) {
         // on-chip: stage the bucket in shared memory
         unsigned char *p = dyn;
-        uint32_t *TB = reinterpret_cast<uint32_t *>(p); p += (size_t)4 * Wn;
+        uint16_t *TB = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * Wn;  // 16-bit element indices
         W *K = reinterpret_cast<W *>(p); p += (size_t)sizeof(W) * cap;
         uint32_t *P = nullptr, *T = nullptr;
         if (a.pay) { P = reinterpret_cast<uint32_t *>(p); p += (size_t)4 * cap; }
@@ -562,8 +654,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
             }
         }
         __syncthreads();
-        BucketView<W, uint16_t> v{K, S16, nullptr, R, F, P, T, X, Y, RL,
-                                  reinterpret_cast<uint16_t *>(TB), Wn - 1u, a.dtype};
+        BucketView<W, uint16_t> v{K, S16, nullptr, R, F, P, T, X, Y, RL, TB, Wn - 1u, a.dtype};
         polish_bucket<W, uint16_t>(a, sm, v, b, s0, nbk, sg);
     } else {
         if (tid == 0) atomicAdd(&a.stats[sm.seg].oversized, 1u);
@@ -762,6 +853,72 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_fix(SolveArgs a) {
         const SeamRange R = a.ranges[r];
         repair_range<W>(a, sm, a.segs[R.seg], R.lo, (uint32_t)(R.hi - R.lo));
     }
+}
+
+// Buckets above POLISH_BIG: k_big_pack copies their partitioned elements (br sorted by position,
+// br[j].off = packed offset) into the packed buffers with the bucket's list index j, or, with
+// unpack = 1, the sorted packed elements to the bucket's output positions; k_big_bounds records
+// each such bucket's first and last output element for the seam.
+template <typename W>
+__global__ void k_big_pack(const BigRange *br, uint32_t nr, const Seg *segs, uint64_t total, const W *sk,
+                           const uint32_t *sp, W *pk, uint32_t *pp, uint32_t *pj, int unpack) {
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (br[mid].off <= q) lo = mid; else hi = mid - 1;
+        }
+        const BigRange r = br[lo];
+        if (!unpack) {
+            const uint64_t e = r.lo + (q - r.off);
+            pk[q] = sk[e];
+            if (pp && sp) pp[q] = sp[e];
+            if (pj) pj[q] = lo;
+        } else {
+            const Seg &sg = segs[r.seg];
+            const uint64_t e = r.lo - sg.ebase + (q - r.off);
+            reinterpret_cast<W *>(sg.keys)[e] = pk[q];
+            if (pp && sg.payload) sg.payload[e] = (int32_t)pp[q];
+        }
+    }
+}
+
+template <typename W>
+__global__ void k_big_bounds(const BigRange *br, uint32_t nr, const Seg *segs, int dtype, OKey *blo,
+                             OKey *bhi) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nr) return;
+    const BigRange r = br[j];
+    const Seg &sg = segs[r.seg];
+    const W *k = reinterpret_cast<const W *>(sg.keys);
+    OKey lo, hi;
+    lo.k = ordbits(word64(k[r.lo - sg.ebase]), dtype); lo.tb = 0; lo.valid = 1;
+    hi.k = ordbits(word64(k[r.hi - 1 - sg.ebase]), dtype); hi.tb = 0; hi.valid = 1;
+    blo[r.b] = lo;
+    bhi[r.b] = hi;
+}
+
+cudaError_t launch_big_pack(const BigRange *br, uint32_t nr, const Seg *segs, uint64_t total, int key_bytes,
+                            const void *src_k, const uint32_t *src_p, void *pk, uint32_t *pp, uint32_t *pj,
+                            int unpack, int sms, cudaStream_t s) {
+    if (total == 0 || nr == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)sms * 8);
+    if (key_bytes == 4)
+        k_big_pack<uint32_t><<<grid, 256, 0, s>>>(br, nr, segs, total, (const uint32_t *)src_k, src_p,
+                                                  (uint32_t *)pk, pp, pj, unpack);
+    else
+        k_big_pack<uint64_t><<<grid, 256, 0, s>>>(br, nr, segs, total, (const uint64_t *)src_k, src_p,
+                                                  (uint64_t *)pk, pp, pj, unpack);
+    return nns_launched(cudaGetLastError());
+}
+
+cudaError_t launch_big_bounds(const BigRange *br, uint32_t nr, const Seg *segs, int key_bytes, int dtype,
+                              OKey *blo, OKey *bhi, cudaStream_t s) {
+    if (nr == 0) return cudaSuccess;
+    if (key_bytes == 4) k_big_bounds<uint32_t><<<(nr + 127) / 128, 128, 0, s>>>(br, nr, segs, dtype, blo, bhi);
+    else k_big_bounds<uint64_t><<<(nr + 127) / 128, 128, 0, s>>>(br, nr, segs, dtype, blo, bhi);
+    return nns_launched(cudaGetLastError());
 }
 
 // Long seam ranges are sorted together: the cut between two ranges is sound, so every element of

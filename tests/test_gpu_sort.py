@@ -375,3 +375,45 @@ def test_batch_long_seams_stay_in_their_array():
         np.testing.assert_array_equal(dp.cpu().numpy(), op)
         assert stats_core(st) == stats_core(ost)
     assert sum(st["repaired"] > 65_536 for st in sts) >= 2
+
+
+# ---------------------------------------------------------------------------- giant buckets
+def test_giant_buckets_sorted_multi_block():
+    """Buckets holding more than 65,536 elements are polished by splitting their runs on chip and
+    sorting their elements in one multi-block sort: outputs, per-iteration counts and out-of-order
+    counts equal the oracle's."""
+    rs = np.random.RandomState(31)
+    n = 400_000
+    keys = W.normal_f32(n, 32)
+    L, _, _ = orc.nm_split(n)
+    rank = np.argsort(np.argsort(keys, kind="stable"), kind="stable")
+    slots = (rank * 5 // 4).astype(np.int64)
+    # two crowded stretches: 25% of the keys on 100 positions, 20% on 3000 positions elsewhere
+    c1 = rs.rand(n) < 0.25
+    slots[c1] = 9000 + (slots[c1] % 100)
+    c2 = (~c1) & (rs.rand(n) < 0.27)
+    slots[c2] = 300_000 + (slots[c2] % 3000)
+    slots = slots.astype(np.uint32)
+    for eps in (1, 3):
+        dk, kt = to_dev(keys)
+        ds = torch.from_numpy(slots.view(np.int32)).cuda()
+        st = nns.sort(dk, None, None, slots=ds, eps=eps, tau=0, key_type=kt, bucket_log2=12)
+        ok, _, ost, _ = orc.nnsort(keys, slots, L, eps, 0)
+        np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+        assert stats_core(st) == stats_core(ost)
+        assert st["oversized_buckets"] >= 2
+    # through a model that sends the lowest 30% of the keys to position 0, with a payload
+    keys = W.uniform_f32(500_000, 33)
+    payload = np.arange(keys.shape[0], dtype=np.int32)
+    nm = orc.make_norm(keys, np.arange(keys.shape[0], dtype=np.uint64), orc.VALUE)
+    p = np.zeros(3 * 8 + 1, np.float32)
+    p[0], p[8], p[16] = 1.0, -0.3, 1.0 / 0.7  # F(x) = relu(x - 0.3) / 0.7
+    om = orc.Model(1, 8, 0, nm, p)
+    dk, _ = to_dev(keys)
+    dp = torch.from_numpy(payload.copy()).cuda()
+    st = nns.sort(dk, dp, lib_model(om))
+    ok, op, ost, _ = orc.nnsort_model(keys, om, payload=payload)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    np.testing.assert_array_equal(dp.cpu().numpy(), op)
+    assert stats_core(st) == stats_core(ost)
+    assert st["oversized_buckets"] >= 1
