@@ -441,6 +441,7 @@ struct Layout {
     SeamRange *ranges; uint32_t *seam_cnt;
     uint32_t *order, *order_cnt;
     BigRange *big; uint32_t *big_cnt;
+    BigRange *giant; uint32_t *giant_cnt; unsigned int *g_cnt, *g_tbmax; unsigned long long *g_kmax;
 };
 
 Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, bool pay, bool rows,
@@ -477,6 +478,11 @@ Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, boo
     L.order_cnt = c.take<uint32_t>(4);
     L.big = c.take<BigRange>(N / POLISH_BIG + 1);
     L.big_cnt = c.take<uint32_t>(4);
+    L.giant = c.take<BigRange>(N / POLISH_BIG + 1);
+    L.giant_cnt = c.take<uint32_t>(4);
+    L.g_cnt = c.take<unsigned int>((N / POLISH_BIG + 1) * MAXR);
+    L.g_tbmax = c.take<unsigned int>((N / POLISH_BIG + 1) * MAXR);
+    L.g_kmax = c.take<unsigned long long>((N / POLISH_BIG + 1) * MAXR);
     *total = align_up(c.off, 256);
     return L;
 }
@@ -866,7 +872,22 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     sa.seam_cnt = L.seam_cnt;
     sa.seam_suf = L.bmax;  // free once the polish has run
     sa.seam_cut = reinterpret_cast<unsigned long long *>(L.carry);
-    CK(launch_bucket_order(L.bstart, P.NB, (uint32_t)sa.polish_cap, L.order, L.order_cnt, s));
+    // buckets above POLISH_BIG elements (possible only when N exceeds it) run their rounds on the
+    // whole GPU; their claim tables reuse the g_x scratch ((N / POLISH_BIG + 1) W entries of 8 bytes
+    // fit in 4 N bytes for N > POLISH_BIG, W <= 2^14), which the polish needs only later
+    GiantRounds gr{};
+    if (P.N > POLISH_BIG) {
+        sa.giant = L.giant;
+        sa.giant_cnt = L.giant_cnt;
+        gr.list = L.giant;
+        gr.count = L.giant_cnt;
+        gr.table = reinterpret_cast<unsigned long long *>(L.g_x);
+        gr.cnt = L.g_cnt;
+        gr.kmax = L.g_kmax;
+        gr.tbmax = L.g_tbmax;
+        gr.cap = (uint32_t)(P.N / POLISH_BIG + 1);
+    }
+    CK(launch_bucket_order(sa, (uint32_t)sa.polish_cap, L.order, L.order_cnt, s));
     sa.order = L.order;
     if (!rows) {
         sa.big = L.big;
@@ -874,6 +895,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
         CK(cudaMemsetAsync(L.big_cnt, 0, sizeof(uint32_t), s));
     }
     CK(launch_rounds(sa, s));
+    if (sa.giant) CK(launch_giant_rounds(sa, gr, o.eps, sm_count(), s));
     CK(mark(4));
     CK(launch_finalize(sa, s));
     CK(mark(5));

@@ -137,13 +137,27 @@ struct SolveArgs {
     OKey *seam_suf;           // [NB] scratch: smallest element of the later buckets
     unsigned long long *seam_cut;  // [2 NB] scratch: first and last sorted-boundary cut per bucket
     const uint32_t *order;    // [NB] nullable: block i of k_rounds / k_polish takes bucket order[i]
+    BigRange *giant;          // nullable: k_bucket_order lists buckets above POLISH_BIG here and
+    uint32_t *giant_cnt;      //   k_rounds leaves them to launch_giant_rounds
     BigRange *big;            // nullable: k_polish lists buckets above POLISH_BIG here (and only
     uint32_t *big_cnt;        //   splits their runs); their sort is left to the host's multi-block sort
 };
 constexpr uint64_t SEAM_CTA_MAX = 1u << 16;  // largest seam repair one block performs
 // order[]: buckets holding more than `heavy` elements first (they run longest), the rest after
-cudaError_t launch_bucket_order(const uint32_t *bstart, uint32_t NB, uint32_t heavy, uint32_t *order,
+cudaError_t launch_bucket_order(const SolveArgs &a, uint32_t heavy, uint32_t *order,
                                 uint32_t *cnt /*[2], zeroed here*/, cudaStream_t s);
+// buckets above POLISH_BIG elements run their rounds on the whole GPU (global claim tables); the
+// list, its count and the per-(bucket, round) statistics live in GiantRounds
+struct GiantRounds {
+    BigRange *list;               // [N / POLISH_BIG + 1]
+    uint32_t *count;              // [1]
+    unsigned long long *table;    // [list entries x W] round-tagged claims
+    unsigned int *cnt;            // [entries x MAXR] elements stored per round
+    unsigned long long *kmax;     // [entries x MAXR] largest order image stored per round
+    unsigned int *tbmax;          // [entries x MAXR] its largest tie-break
+    uint32_t cap;                 // list entries
+};
+cudaError_t launch_giant_rounds(const SolveArgs &a, const GiantRounds &g, int eps, int sms, cudaStream_t s);
 cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s);

@@ -57,20 +57,151 @@ __device__ __forceinline__ KMax kmax_none() { KMax r; r.k = 0; r.tb = 0; r.valid
 // Bucket order for the per-bucket kernels: blocks are dispatched roughly in index order, so heavy
 // buckets listed first start first and run alongside the many light ones instead of forming a
 // tail. Heavy buckets fill order[] from the front, light ones from the back.
-__global__ void k_bucket_order(const uint32_t *bstart, uint32_t NB, uint32_t heavy, uint32_t *order,
-                               uint32_t *cnt) {
+__global__ void k_bucket_order(SolveArgs a, uint32_t heavy, uint32_t *order, uint32_t *cnt) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= NB) return;
-    if (bstart[b + 1] - bstart[b] > heavy) order[atomicAdd(&cnt[0], 1u)] = b;
-    else order[NB - 1 - atomicAdd(&cnt[1], 1u)] = b;
+    if (b >= a.NB) return;
+    const uint32_t nbk = a.bstart[b + 1] - a.bstart[b];
+    if (nbk > heavy) order[atomicAdd(&cnt[0], 1u)] = b;
+    else order[a.NB - 1 - atomicAdd(&cnt[1], 1u)] = b;
+    if (a.giant && nbk > POLISH_BIG) {
+        BigRange r;
+        r.lo = a.bstart[b]; r.hi = a.bstart[b + 1];
+        r.seg = (uint32_t)seg_of_bucket(a.segs, a.nseg, b); r.off = 0; r.b = b; r.pad = 0;
+        a.giant[atomicAdd(a.giant_cnt, 1u)] = r;
+    }
 }
 
-cudaError_t launch_bucket_order(const uint32_t *bstart, uint32_t NB, uint32_t heavy, uint32_t *order,
-                                uint32_t *cnt, cudaStream_t s) {
-    if (NB == 0) return cudaSuccess;
+cudaError_t launch_bucket_order(const SolveArgs &a, uint32_t heavy, uint32_t *order, uint32_t *cnt,
+                                cudaStream_t s) {
+    if (a.NB == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), s);
+    if (e == cudaSuccess && a.giant_cnt) e = cudaMemsetAsync(a.giant_cnt, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_bucket_order<<<(NB + 255) / 256, 256, 0, s>>>(bstart, NB, heavy, order, cnt);
+    k_bucket_order<<<(a.NB + 255) / 256, 256, 0, s>>>(a, heavy, order, cnt);
+    return nns_launched(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------------
+// Rounds of buckets above POLISH_BIG elements, spread over the whole GPU: the same first-arrival
+// rule with the claims in a global table per bucket. A claim in round r stores (MAXR - r) << 32 | i,
+// so one atomicMin both picks the lowest row among round-r claimants and overrides the entries of
+// earlier rounds; the table is cleared once. Every kernel walks the listed buckets in turn, each
+// bucket's elements spread over all threads (consecutive elements on consecutive lanes).
+template <typename Fn>
+__device__ __forceinline__ void giant_walk(const GiantRounds &g, Fn fn) {
+    const uint32_t nb = *g.count;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t j = 0; j < nb; ++j) {
+        const BigRange r = g.list[j];
+        const uint64_t len = r.hi - r.lo;
+        // a uniform trip count per warp, so that warp-wide intrinsics see all lanes
+        for (uint64_t base = t0 & ~31ull; base < len; base += stride) fn(j, r, base + (t0 & 31), len);
+    }
+}
+
+__global__ void k_giant_init(SolveArgs a, GiantRounds g) {
+    const uint32_t nb = *g.count;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t Wn = 1ull << a.wlog;
+    for (uint64_t q = t0; q < (uint64_t)nb * Wn; q += stride) g.table[q] = ~0ull;
+    for (uint64_t q = t0; q < (uint64_t)nb * MAXR; q += stride) { g.cnt[q] = 0; g.kmax[q] = 0; g.tbmax[q] = 0; }
+    giant_walk(g, [&](uint32_t, const BigRange &r, uint64_t i, uint64_t len) {
+        if (i < len) a.rank[r.lo + i] = 0;
+    });
+}
+
+__global__ void k_giant_claim(SolveArgs a, GiantRounds g, int r) {
+    const uint32_t wm = (1u << a.wlog) - 1u;
+    const unsigned lanes_below = (1u << (threadIdx.x & 31)) - 1u;
+    const unsigned long long tag = (unsigned long long)(MAXR - r) << 32;
+    giant_walk(g, [&](uint32_t j, const BigRange &rg, uint64_t i, uint64_t len) {
+        const bool act = i < len && a.rank[rg.lo + i] == r;
+        const uint32_t p = act ? (a.gs[rg.lo + i] & wm) : EMPTY32;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, p);
+        if (act && (peers & lanes_below) == 0)
+            atomicMin(&g.table[((uint64_t)j << a.wlog) + p], tag | (unsigned long long)i);
+    });
+}
+
+__global__ void k_giant_check(SolveArgs a, GiantRounds g, int r) {
+    const uint32_t wm = (1u << a.wlog) - 1u;
+    const unsigned long long tag = (unsigned long long)(MAXR - r) << 32;
+    giant_walk(g, [&](uint32_t j, const BigRange &rg, uint64_t i, uint64_t len) {
+        if (i < len && a.rank[rg.lo + i] == r) {
+            const uint32_t p = a.gs[rg.lo + i] & wm;
+            if (g.table[((uint64_t)j << a.wlog) + p] != (tag | (unsigned long long)i))
+                a.rank[rg.lo + i] = (uint8_t)(r + 1);
+        }
+    });
+}
+
+// per (bucket, round): how many elements were stored and the largest order image among them
+template <typename W>
+__global__ void k_giant_stats(SolveArgs a, GiantRounds g, int eps) {
+    giant_walk(g, [&](uint32_t j, const BigRange &rg, uint64_t i, uint64_t len) {
+        if (i >= len) return;
+        const int c = a.rank[rg.lo + i];
+        if (c >= eps) return;
+        const unsigned long long k = ordbits(word64(ldk<W>(a.keys, rg.lo + i)), a.dtype);
+        atomicAdd(&g.cnt[j * MAXR + c], 1u);
+        atomicMax(&g.kmax[j * MAXR + c], k);
+    });
+}
+
+// the largest tie-break among the stored elements with that order image
+template <typename W>
+__global__ void k_giant_stats2(SolveArgs a, GiantRounds g, int eps) {
+    giant_walk(g, [&](uint32_t j, const BigRange &rg, uint64_t i, uint64_t len) {
+        if (i >= len) return;
+        const int c = a.rank[rg.lo + i];
+        if (c >= eps) return;
+        const unsigned long long k = ordbits(word64(ldk<W>(a.keys, rg.lo + i)), a.dtype);
+        if (k == g.kmax[j * MAXR + c])
+            atomicMax(&g.tbmax[j * MAXR + c], a.rows ? a.rows[rg.lo + i] : (uint32_t)i);
+    });
+}
+
+__global__ void k_giant_fin(SolveArgs a, GiantRounds g, int eps) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *g.count) return;
+    const BigRange rg = g.list[j];
+    unsigned long long ge = rg.hi - rg.lo;
+    for (int r = 0; r < eps; ++r) {
+        const unsigned int c = g.cnt[j * MAXR + r];
+        ge -= c;
+        if (ge) atomicAdd(&a.stats[rg.seg].count_ge[r + 1], ge);
+        OKey o;
+        o.k = c ? g.kmax[j * MAXR + r] : 0ull;
+        o.tb = c ? g.tbmax[j * MAXR + r] : 0u;
+        o.valid = c ? 1u : 0u;
+        a.bmax[(size_t)rg.b * MAXR + r] = o;
+    }
+}
+
+cudaError_t launch_giant_rounds(const SolveArgs &a, const GiantRounds &g, int eps, int sms, cudaStream_t s) {
+    const unsigned grid = (unsigned)sms * 4, th = 256;
+    cudaError_t e;
+    k_giant_init<<<grid, th, 0, s>>>(a, g);
+    if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    for (int r = 0; r < eps; ++r) {
+        k_giant_claim<<<grid, th, 0, s>>>(a, g, r);
+        if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+        k_giant_check<<<grid, th, 0, s>>>(a, g, r);
+        if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    }
+    if (a.key_bytes == 4) {
+        k_giant_stats<uint32_t><<<grid, th, 0, s>>>(a, g, eps);
+        if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+        k_giant_stats2<uint32_t><<<grid, th, 0, s>>>(a, g, eps);
+    } else {
+        k_giant_stats<uint64_t><<<grid, th, 0, s>>>(a, g, eps);
+        if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+        k_giant_stats2<uint64_t><<<grid, th, 0, s>>>(a, g, eps);
+    }
+    if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    k_giant_fin<<<(g.cap + 127) / 128, 128, 0, s>>>(a, g, eps);
     return nns_launched(cudaGetLastError());
 }
 
@@ -101,6 +232,7 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
         if (tid < MAXR) { OKey z; z.k = 0; z.tb = 0; z.valid = 0; a.bmax[(size_t)b * MAXR + tid] = z; }
         return;
     }
+    if (a.giant && nbk > POLISH_BIG) return;  // launch_giant_rounds
     if (tid == 0) sh_seg = seg_of_bucket(a.segs, a.nseg, b);
     __syncthreads();
     const int seg = sh_seg;

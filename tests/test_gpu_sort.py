@@ -402,6 +402,9 @@ def test_giant_buckets_sorted_multi_block():
         np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
         assert stats_core(st) == stats_core(ost)
         assert st["oversized_buckets"] >= 2
+    # with a payload and the per-row fates (rows are carried: the rounds of giant buckets use rows as
+    # the tie-break, their polish stays on one block)
+    _check_injected(keys, slots, L, 3, 0, payload=np.arange(n, dtype=np.int32), bucket_log2=12)
     # through a model that sends the lowest 30% of the keys to position 0, with a payload
     keys = W.uniform_f32(500_000, 33)
     payload = np.arange(keys.shape[0], dtype=np.int32)
