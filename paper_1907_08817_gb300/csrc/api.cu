@@ -871,6 +871,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     sa.max_ranges = P.NB + (uint32_t)nseg;
     sa.seam_cnt = L.seam_cnt;
     sa.seam_suf = L.bmax;  // free once the polish has run
+    sa.seam_pre = L.bmax + P.NB;
     sa.seam_cut = reinterpret_cast<unsigned long long *>(L.carry);
     // buckets above POLISH_BIG elements (possible only when N exceeds it) run their rounds on the
     // whole GPU; their claim tables reuse the g_x scratch ((N / POLISH_BIG + 1) W entries of 8 bytes

@@ -135,6 +135,7 @@ struct SolveArgs {
     uint32_t max_ranges;      // >= NB + nseg
     uint32_t *seam_cnt;       // [4]: block-sized ranges, large ranges, next range to repair
     OKey *seam_suf;           // [NB] scratch: smallest element of the later buckets
+    OKey *seam_pre;           // [NB] scratch: largest element of the earlier buckets
     unsigned long long *seam_cut;  // [2 NB] scratch: first and last sorted-boundary cut per bucket
     const uint32_t *order;    // [NB] nullable: block i of k_rounds / k_polish takes bucket order[i]
     BigRange *giant;          // nullable: k_bucket_order lists buckets above POLISH_BIG here and

@@ -808,8 +808,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
 // sorted elements e_0 <= ... <= e_{len-1}, preceded by elements whose maximum is P and followed by
 // elements whose minimum is S, the cut before e_j is sound iff P <= S and P <= e_j and
 // e_{j-1} <= S; with P <= S these hold for j in [#{e < P}, #{e <= S}], a non-empty interval.
-//   k_seam_scan  -- one block per array: per bucket the first and last sound cut, then the runs
-//                   between consecutive sound cuts that hold two or more elements.
+//   k_seam_ps / k_seam_cuts / k_seam_emit -- per bucket the largest element before it and the
+//                   smallest after it, its first and last sound cut, then the runs between
+//                   consecutive sound cuts that hold two or more elements.
 //   k_seam_fix   -- blocks take the runs of at most SEAM_CTA_MAX elements one by one and sort each
 //                   on chip; longer runs go to the multi-block sort on the host's side (or are
 //                   sorted here too when rows are carried or deferral is off).
@@ -817,89 +818,112 @@ __device__ __forceinline__ KMax kinv(const KMax &x) {
     KMax r; r.k = ~x.k; r.tb = ~x.tb; r.valid = x.valid; return r;
 }
 
-template <typename W>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_seam_scan(SolveArgs a) {
+// Scans over an array's buckets walk tiles of SOLVE_THREADS consecutive buckets (one per thread,
+// coalesced loads) with the running value carried from tile to tile; a backward scan gives thread
+// t the bucket tile_end - 1 - t, so that an exclusive scan over threads runs over later buckets.
+// 1) k_seam_ps (one block per array): S(b) = the smallest element of the buckets after b,
+//    P(b) = the largest element of the buckets before b.
+__global__ void __launch_bounds__(SOLVE_THREADS) k_seam_ps(SolveArgs a) {
     __shared__ KMax ks[33];
     __shared__ KMax tot;
     const int s = blockIdx.x, tid = threadIdx.x;
     if (*a.err) return;
     const Seg &sg = a.segs[s];
-    const int dt = a.dtype;
-    const W *outk = reinterpret_cast<const W *>(sg.keys);
     const uint32_t nb = sg.nb, bb = sg.bbase;
-    const unsigned long long n = sg.n, NONE = ~0ull;
-    const uint32_t per = (nb + SOLVE_THREADS - 1) / SOLVE_THREADS;
-    // own chunk for forward passes, mirrored chunk for backward passes
-    const uint32_t c0 = min(nb, tid * per), c1 = min(nb, c0 + per);
-    const uint32_t mt = SOLVE_THREADS - 1 - tid;
-    const uint32_t m0 = min(nb, mt * per), m1 = min(nb, m0 + per);
-    auto bstart = [&](uint32_t bi) -> unsigned long long { return a.bstart[bi] - sg.ebase; };
-    auto nonempty = [&](uint32_t bi) { return a.bstart[bi + 1] > a.bstart[bi]; };
+    auto okey = [&](const OKey &o) { KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid; return x; };
+    KMax carry = kmax_none();  // inverted minimum of the buckets after the current tile
+    for (uint32_t t1 = nb; t1 > 0;) {
+        const uint32_t t0 = t1 > SOLVE_THREADS ? t1 - SOLVE_THREADS : 0;
+        const uint32_t c = t1 - 1 - tid;  // this thread's bucket (valid when tid < t1 - t0)
+        const bool own = (uint32_t)tid < t1 - t0;
+        const uint32_t bi = bb + c;
+        const bool ne = own && a.bstart[bi + 1] > a.bstart[bi];
+        const KMax v = ne ? kinv(okey(a.blo[bi])) : kmax_none();
+        const KMax ex = block_excl_max(v, ks, &tot);
+        if (ne) {
+            const KMax sv = kinv(kmax(carry, ex));
+            OKey o; o.k = sv.k; o.tb = sv.tb; o.valid = sv.valid;
+            a.seam_suf[bi] = o;
+        }
+        carry = kmax(carry, tot);
+        t1 = t0;
+    }
+    carry = kmax_none();  // maximum of the buckets before the current tile
+    for (uint32_t t0 = 0; t0 < nb; t0 += SOLVE_THREADS) {
+        const uint32_t c = t0 + tid;
+        const bool own = c < nb;
+        const uint32_t bi = bb + c;
+        const bool ne = own && a.bstart[bi + 1] > a.bstart[bi];
+        const KMax v = ne ? okey(a.bhi[bi]) : kmax_none();
+        const KMax ex = block_excl_max(v, ks, &tot);
+        if (ne) {
+            const KMax pv = kmax(carry, ex);
+            OKey o; o.k = pv.k; o.tb = pv.tb; o.valid = pv.valid;
+            a.seam_pre[bi] = o;
+        }
+        carry = kmax(carry, tot);
+    }
+}
+
+// 2) k_seam_cuts (one thread per bucket of every array): the bucket's first and last sound cut.
+template <typename W>
+__global__ void k_seam_cuts(SolveArgs a) {
+    const uint32_t bi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bi >= a.NB || *a.err) return;
+    const unsigned long long NONE = ~0ull;
+    if (a.bstart[bi + 1] == a.bstart[bi]) {
+        a.seam_cut[2 * (size_t)bi] = NONE;
+        a.seam_cut[2 * (size_t)bi + 1] = NONE;
+        return;
+    }
+    const Seg &sg = a.segs[seg_of_bucket(a.segs, a.nseg, bi)];
+    const W *outk = reinterpret_cast<const W *>(sg.keys);
     auto okey = [&](const OKey &o) { KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid; return x; };
     auto elem = [&](unsigned long long pos, unsigned long long &k, uint32_t &tb) {
-        k = ordbits(word64(outk[pos]), dt);
+        k = ordbits(word64(outk[pos]), a.dtype);
         tb = a.out_rows ? a.out_rows[sg.ebase + pos] : 0u;
     };
-
-    // 1) S(b): the smallest element of the buckets after b (backward over the mirrored chunks)
-    KMax loc = kmax_none();
-    for (uint32_t c = m0; c < m1; ++c)
-        if (nonempty(bb + c)) loc = kmax(loc, kinv(okey(a.blo[bb + c])));
-    KMax run = block_excl_max(loc, ks, nullptr);  // over the chunks after this one
-    for (uint32_t c = m1; c > m0; --c) {
-        const uint32_t bi = bb + c - 1;
-        if (!nonempty(bi)) continue;
-        const KMax sv = kinv(run);
-        OKey o; o.k = sv.k; o.tb = sv.tb; o.valid = sv.valid;
-        a.seam_suf[bi] = o;
-        run = kmax(run, kinv(okey(a.blo[bi])));
-    }
-    __syncthreads();
-
-    // 2) P(b): the largest element of the buckets before b; the bucket's sound cuts
-    loc = kmax_none();
-    for (uint32_t c = c0; c < c1; ++c)
-        if (nonempty(bb + c)) loc = kmax(loc, okey(a.bhi[bb + c]));
-    run = block_excl_max(loc, ks, nullptr);
-    for (uint32_t c = c0; c < c1; ++c) {
-        const uint32_t bi = bb + c;
-        if (!nonempty(bi)) continue;
-        const KMax P = run, S = okey(a.seam_suf[bi]);
-        const unsigned long long b0 = bstart(bi), b1 = bstart(bi + 1);
-        unsigned long long fg = NONE, lg = NONE;
-        if (!(P.valid && S.valid && okey_less(S.k, S.tb, P.k, P.tb))) {
-            // A = #{e < P}
-            unsigned long long l = b0, h = b1;
-            if (P.valid) {
-                while (l < h) {
-                    const unsigned long long mid = (l + h) >> 1;
-                    unsigned long long k; uint32_t tb;
-                    elem(mid, k, tb);
-                    if (okey_less(k, tb, P.k, P.tb)) l = mid + 1; else h = mid;
-                }
+    const KMax P = okey(a.seam_pre[bi]), S = okey(a.seam_suf[bi]);
+    const unsigned long long b0 = a.bstart[bi] - sg.ebase, b1 = a.bstart[bi + 1] - sg.ebase;
+    unsigned long long fg = NONE, lg = NONE;
+    if (!(P.valid && S.valid && okey_less(S.k, S.tb, P.k, P.tb))) {
+        unsigned long long l = b0, h = b1;  // A = #{e < P}
+        if (P.valid) {
+            while (l < h) {
+                const unsigned long long mid = (l + h) >> 1;
+                unsigned long long k; uint32_t tb;
+                elem(mid, k, tb);
+                if (okey_less(k, tb, P.k, P.tb)) l = mid + 1; else h = mid;
             }
-            fg = l;
-            // B = #{e <= S}
-            l = fg; h = b1;
-            if (S.valid) {
-                while (l < h) {
-                    const unsigned long long mid = (l + h) >> 1;
-                    unsigned long long k; uint32_t tb;
-                    elem(mid, k, tb);
-                    if (!okey_less(S.k, S.tb, k, tb)) l = mid + 1; else h = mid;
-                }
-            } else {
-                l = b1;
-            }
-            lg = l;
         }
-        a.seam_cut[2 * (size_t)bi] = fg;
-        a.seam_cut[2 * (size_t)bi + 1] = lg;
-        run = kmax(run, okey(a.bhi[bi]));
+        fg = l;
+        l = fg; h = b1;  // B = #{e <= S}
+        if (S.valid) {
+            while (l < h) {
+                const unsigned long long mid = (l + h) >> 1;
+                unsigned long long k; uint32_t tb;
+                elem(mid, k, tb);
+                if (!okey_less(S.k, S.tb, k, tb)) l = mid + 1; else h = mid;
+            }
+        } else {
+            l = b1;
+        }
+        lg = l;
     }
-    __syncthreads();
+    a.seam_cut[2 * (size_t)bi] = fg;
+    a.seam_cut[2 * (size_t)bi + 1] = lg;
+}
 
-    // 3) runs between consecutive sound cuts (backward: the next bucket's first sound cut)
+// 3) k_seam_emit (one block per array): the runs between consecutive sound cuts that hold two or
+//    more elements (backward: the next bucket's first sound cut).
+__global__ void __launch_bounds__(SOLVE_THREADS) k_seam_emit(SolveArgs a) {
+    __shared__ KMax ks[33];
+    __shared__ KMax tot;
+    const int s = blockIdx.x, tid = threadIdx.x;
+    if (*a.err) return;
+    const Seg &sg = a.segs[s];
+    const uint32_t nb = sg.nb, bb = sg.bbase;
+    const unsigned long long n = sg.n, NONE = ~0ull;
     auto emit = [&](unsigned long long lo, unsigned long long hi) {
         if (hi - lo < 2) return;
         atomicAdd(&a.stats[s].repaired, hi - lo);
@@ -912,21 +936,22 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_scan(SolveArgs a) {
             a.ranges[atomicAdd(&a.seam_cnt[0], 1u)] = r;
         }
     };
-    loc = kmax_none();  // the smallest first sound cut of the chunk, as an inverted maximum
-    for (uint32_t c = m0; c < m1; ++c) {
-        const unsigned long long fg = nonempty(bb + c) ? a.seam_cut[2 * (size_t)(bb + c)] : NONE;
-        if (fg != NONE) { KMax x; x.k = ~fg; x.tb = 0; x.valid = 1; loc = kmax(loc, x); }
+    KMax carry = kmax_none();  // smallest first sound cut after the current tile (inverted)
+    for (uint32_t t1 = nb; t1 > 0;) {
+        const uint32_t t0 = t1 > SOLVE_THREADS ? t1 - SOLVE_THREADS : 0;
+        const uint32_t c = t1 - 1 - tid;
+        const bool own = (uint32_t)tid < t1 - t0;
+        const uint32_t bi = bb + c;
+        const unsigned long long fg = own ? a.seam_cut[2 * (size_t)bi] : NONE;
+        const unsigned long long lg = own ? a.seam_cut[2 * (size_t)bi + 1] : NONE;
+        KMax v = kmax_none();
+        if (fg != NONE) { v.k = ~fg; v.tb = 0; v.valid = 1; }
+        const KMax ex = kmax(carry, block_excl_max(v, ks, &tot));
+        if (lg != NONE) emit(lg, ex.valid ? ~ex.k : n);
+        carry = kmax(carry, tot);
+        t1 = t0;
     }
-    run = block_excl_max(loc, ks, &tot);
-    unsigned long long nf = run.valid ? ~run.k : n;
-    for (uint32_t c = m1; c > m0; --c) {
-        const uint32_t bi = bb + c - 1;
-        if (!nonempty(bi)) continue;
-        const unsigned long long fg = a.seam_cut[2 * (size_t)bi], lg = a.seam_cut[2 * (size_t)bi + 1];
-        if (lg != NONE) emit(lg, nf);
-        if (fg != NONE) nf = fg;
-    }
-    if (tid == 0) emit(0, tot.valid ? ~tot.k : n);  // before the first sound cut
+    if (tid == 0) emit(0, carry.valid ? ~carry.k : n);  // before the first sound cut
 }
 
 // re-sort out[lo, lo + len) of one array by (key, row): the range is a union of sorted runs
@@ -1128,7 +1153,11 @@ cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s) {
 template <typename W> static cudaError_t seam_go(const SolveArgs &a, int sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.seam_cnt, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_seam_scan<W><<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
+    k_seam_ps<<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
+    if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    k_seam_cuts<W><<<(a.NB + 255) / 256, 256, 0, s>>>(a);
+    if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    k_seam_emit<<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
     k_seam_fix<W><<<2 * sms, SOLVE_THREADS, sizeof(PolishSmem), s>>>(a);
     return nns_launched(cudaGetLastError());

@@ -190,6 +190,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     const uint64_t total = (uint64_t)a.total_tiles * sub_per_tile;
     const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
     const uint32_t aoff = (tid / 8) * SBO + (tid % 8) * 16;  // this thread's row in an A tile
+    // the next sub-tile's keys are loaded while this one is computed (when it lies in the same array)
+    uint64_t pre[KPT];
+    uint64_t pre_st = ~0ull;
 
     for (uint64_t st = blockIdx.x; st < total; st += gridDim.x) {
         const uint32_t tile = (uint32_t)(st / sub_per_tile), sub = (uint32_t)(st % sub_per_tile);
@@ -228,8 +231,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
         for (int g = 0; g < KPT; ++g) {
             const uint64_t i = r0 + (uint64_t)g * TC_M + tid;
             valid[g] = i < n;
-            wv[g] = valid[g] ? word64(keys[i]) : 0ull;
+            wv[g] = !valid[g] ? 0ull : (pre_st == st ? pre[g] : word64(keys[i]));
             if (valid[g] && key_is_nan(wv[g], a.dtype)) err |= ERR_NAN;
+        }
+        {
+            const uint64_t st2 = st + gridDim.x;
+            const uint32_t tile2 = (uint32_t)(st2 / sub_per_tile), sub2 = (uint32_t)(st2 % sub_per_tile);
+            if (st2 < total && tile2 < sg.tbase + sg.ntiles) {
+                const uint64_t q0 = (uint64_t)(tile2 - sg.tbase) * PRED_TILE + (uint64_t)sub2 * SUB;
+#pragma unroll
+                for (int g = 0; g < KPT; ++g) {
+                    const uint64_t i = q0 + (uint64_t)g * TC_M + tid;
+                    pre[g] = i < n ? word64(keys[i]) : 0ull;
+                }
+                pre_st = st2;
+            }
         }
         float y[KPT];
         uint32_t slot[KPT];
@@ -395,14 +411,17 @@ static cudaError_t bf16_go(const PredictArgs &p, int sms, cudaStream_t s) {
     return nns_launched(cudaGetLastError());
 }
 
-constexpr int TC_KPT = 2;  // keys per thread per sub-tile
+// keys per thread per sub-tile: two for the plain form (parameter reads shared by two keys, 4 blocks
+// per SM); one for the split form, whose second A tile would otherwise halve the resident blocks
+// (measured at 2^28 keys, H = 64: split 12.1 ms at one key vs 15.9 ms at two; plain 8.1 vs 8.3 ms)
+constexpr int TC_KPT = 2, TC_KPT_SPLIT = 1;
 
 cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, bool split, int sms, cudaStream_t s) {
     if (a.layers != 2) return cudaErrorNotSupported;
     switch (a.h1) {
-    case 16: return split ? bf16_go<16, true, TC_KPT>(p, sms, s) : bf16_go<16, false, TC_KPT>(p, sms, s);
-    case 32: return split ? bf16_go<32, true, TC_KPT>(p, sms, s) : bf16_go<32, false, TC_KPT>(p, sms, s);
-    case 64: return split ? bf16_go<64, true, TC_KPT>(p, sms, s) : bf16_go<64, false, TC_KPT>(p, sms, s);
+    case 16: return split ? bf16_go<16, true, TC_KPT_SPLIT>(p, sms, s) : bf16_go<16, false, TC_KPT>(p, sms, s);
+    case 32: return split ? bf16_go<32, true, TC_KPT_SPLIT>(p, sms, s) : bf16_go<32, false, TC_KPT>(p, sms, s);
+    case 64: return split ? bf16_go<64, true, TC_KPT_SPLIT>(p, sms, s) : bf16_go<64, false, TC_KPT>(p, sms, s);
     }
     return cudaErrorNotSupported;  // widths below 16 stay on the binary32 path
 }

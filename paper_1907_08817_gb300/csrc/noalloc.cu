@@ -269,6 +269,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     sa.max_ranges = sg.nb + 1;
     sa.seam_cnt = L.seam_cnt;
     sa.seam_suf = L.bmax;
+    sa.seam_pre = L.bmax + sg.nb;
     sa.seam_cut = reinterpret_cast<unsigned long long *>(L.carry);
     NA_CK(launch_rounds(sa, s));
     NA_CK(launch_finalize(sa, s));
