@@ -63,10 +63,11 @@ typedef enum { NNSORT_TRANSLATE_ORDBITS = 0, NNSORT_TRANSLATE_VALUE = 1 } nnsort
 /* Arithmetic of the model's forward pass inside a sort. FP32: binary32 FMA chains, bit-identical
  * to the CPU reference. BF16: the hidden-to-hidden layer runs on the tensor cores (tcgen05, BF16
  * operands, FP32 accumulation); first and output layers stay binary32. BF16X2: as BF16, but each
- * first-layer activation h is passed as the pair hi = bf16(h), lo = bf16(h - hi), both multiplied
- * by the BF16 weights into the same FP32 accumulator (two MMAs): the activations keep ~16
- * significant bits, so F stays as finely resolved in x as the binary32 model (the weights'
- * rounding only changes f smoothly). Two-hidden-layer models only; others use binary32. */
+ * first-layer activation a is passed as the pair hi = a truncated to BF16, lo = (a - hi) rounded to
+ * FP16; hi multiplies the BF16 weights and lo an FP16 copy of them, into the same FP32 accumulator
+ * (two MMA chains): the activations keep ~19 significant bits, so F stays about as finely resolved
+ * in x as the binary32 model (the weights' rounding only changes f smoothly). Two-hidden-layer
+ * models only; others use binary32. */
 typedef enum { NNSORT_PREC_FP32 = 0, NNSORT_PREC_BF16 = 1, NNSORT_PREC_BF16X2 = 2 } nnsort_precision;
 
 /* Training loss: mean squared error, or the Huber loss of Eq. (loss). */

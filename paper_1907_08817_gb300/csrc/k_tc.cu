@@ -3,8 +3,9 @@
 //
 // Per sub-tile of KPT x 128 keys (KPT keys per thread, 4 warps):
 //   layer 1 (1 -> H)  binary32 FFMA, ReLU, rounded to BF16 and stored as the A operand
-//                     (128 x H, K-major, no swizzle: 8x8 core matrices of 128 bytes); with the
-//                     split form also the rounding residual, rounded to BF16, as a second A tile;
+//                     (128 x H, K-major, no swizzle: 8x8 core matrices of 128 bytes); the split form
+//                     stores ReLU(h) truncated to BF16 and the (exact, non-negative) rest rounded to
+//                     FP16 as a second A tile, multiplied by an FP16 copy of W2;
 //   layer 2 (H -> H)  tcgen05.mma.kind::f16, M = 128, N = H, K = H in steps of 16, issued by one
 //                     thread; B = W2 (H x H, K-major) staged once per block; D in TMEM (the split
 //                     form accumulates A_hi W2^T + A_lo W2^T into the same D);
@@ -13,6 +14,7 @@
 // The MMA completion is signalled through an mbarrier whose wait gives up after a time limit
 // (the kernel then raises ERR_TIMEOUT, still frees its tensor memory and returns).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -46,6 +48,10 @@ __device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t
 
 // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = BF16 (bits 7-9 = 1),
 // B = BF16 (bits 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28
+// instruction descriptor, kind::f16 with A = B = F16 (type code 0 in bits 7-9 and 10-12)
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -73,6 +79,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if (globaltimer_ns() - t0 > SPIN_LIMIT_NS) return false;
     }
     return true;
+}
+
+// two binary32 values packed as BF16 (first value in the low half), negative results set to 0
+__device__ __forceinline__ uint32_t cvt_bf16x2_rn_relu(float first, float second) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(second), "f"(first));
+    return d;
+}
+__device__ __forceinline__ uint32_t cvt_f16x2_rn_relu(float first, float second) {
+    uint32_t d;
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(second), "f"(first));
+    return d;
+}
+__device__ __forceinline__ uint32_t cvt_bf16x2_rz_relu(float first, float second) {
+    uint32_t d;
+    asm("cvt.rz.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(second), "f"(first));
+    return d;
 }
 
 __device__ __forceinline__ void fence_async_smem() {
@@ -145,8 +168,8 @@ __host__ __device__ constexpr int tc_ncol(int H, int KPT) {
 }
 template <int H, bool SPLIT, int KPT>
 __host__ __device__ constexpr size_t tc_smem_bytes(int npass) {
-    return (size_t)KPT * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)H * H * 2 + (size_t)(4 * H + 4) * 4 +
-           (size_t)npass * RADIX_BINS * 4;
+    return (size_t)KPT * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)(SPLIT ? 2 : 1) * H * H * 2 +
+           (size_t)(4 * H + 4) * 4 + (size_t)npass * RADIX_BINS * 4;
 }
 
 template <int H, typename W, bool SPLIT, int KPT>
@@ -161,7 +184,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     constexpr int SUB = KPT * TC_M;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sB = sm + KPT * NT * TILE_B;                       // H x H bf16
-    float *pf = reinterpret_cast<float *>(sB + H * H * 2);            // W1 | b1 | b2 | W3 | b3
+    unsigned char *sB16 = sB + H * H * 2;                             // H x H fp16 (split form)
+    float *pf = reinterpret_cast<float *>(sB + (SPLIT ? 2 : 1) * H * H * 2);  // W1 | b1 | b2 | W3 | b3
     const float4 *pv = reinterpret_cast<const float4 *>(pf);
     uint32_t *sh_hist = reinterpret_cast<uint32_t *>(pf + 4 * H + 4);
     __shared__ __align__(8) unsigned long long bar;
@@ -181,6 +205,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     tc_fence_after();
     const uint32_t tbase = tmem_base;
     const uint32_t idesc = idesc_bf16(TC_M, H);
+    const uint32_t idesc_lo = idesc_f16(TC_M, H);
     uint32_t phase = 0;
     uint32_t err = 0;
     bool dead = false;  // set once a wait gave up: no further MMAs are issued
@@ -212,6 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                 const int nrow = e / H, k = e % H;
                 const uint32_t off = (nrow / 8) * SBO + (k / 8) * LBO + (nrow % 8) * 16 + (k % 8) * 2;
                 *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16_rn(W2[e]);
+                if (SPLIT) *reinterpret_cast<__half *>(sB16 + off) = __float2half_rn(W2[e]);
             }
             for (int e = tid; e < H; e += TC_THREADS) {
                 pf[e] = sg.params[e];                          // W1
@@ -267,14 +293,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                     uint32_t hi[4], lo[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float h0 = relu_f(__fmaf_rn(w8[2 * q], x[g], b8[2 * q]));
-                        const float h1 = relu_f(__fmaf_rn(w8[2 * q + 1], x[g], b8[2 * q + 1]));
-                        const __nv_bfloat162 p = __floats2bfloat162_rn(h0, h1);
-                        hi[q] = *reinterpret_cast<const uint32_t *>(&p);
-                        if (SPLIT) {
-                            const float2 f = __bfloat1622float2(p);
-                            const __nv_bfloat162 r = __floats2bfloat162_rn(__fsub_rn(h0, f.x), __fsub_rn(h1, f.y));
-                            lo[q] = *reinterpret_cast<const uint32_t *>(&r);
+                        // pre-activations; the conversions apply the ReLU (negative results become 0)
+                        const float h0 = __fmaf_rn(w8[2 * q], x[g], b8[2 * q]);
+                        const float h1 = __fmaf_rn(w8[2 * q + 1], x[g], b8[2 * q + 1]);
+                        if (!SPLIT) {
+                            hi[q] = cvt_bf16x2_rn_relu(h0, h1);  // RN(ReLU(h))
+                        } else {
+                            // ReLU(h) = hi + lo: hi = ReLU(h) truncated to BF16 (8 significant bits),
+                            // lo = the rest (non-negative, exact in binary32) rounded to FP16 (11
+                            // bits); for h <= 0 both parts are 0
+                            hi[q] = cvt_bf16x2_rz_relu(h0, h1);
+                            const float r0 = __fsub_rn(h0, __uint_as_float(__float_as_uint(h0) & 0xFFFF0000u));
+                            const float r1 = __fsub_rn(h1, __uint_as_float(__float_as_uint(h1) & 0xFFFF0000u));
+                            lo[q] = cvt_f16x2_rn_relu(r0, r1);
                         }
                     }
                     unsigned char *t0 = sm + (g * NT) * TILE_B + aoff + (j0 / 8) * LBO;
@@ -299,7 +330,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
 #pragma unroll
                         for (int ks = 0; ks < H / 16; ++ks)
                             mma_bf16(tbase + g * H, mdesc(a0 + TILE_B + ks * 2 * LBO, LBO, SBO),
-                                     mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc, 1u);
+                                     mdesc(smem_u32(sB16) + ks * 2 * LBO, LBO, SBO), idesc_lo, 1u);
                     }
                 }
                 mma_commit(smem_u32(&bar));

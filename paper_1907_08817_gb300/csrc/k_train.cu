@@ -525,16 +525,38 @@ struct ReduceArgs {
     float lr, b1, b2, eps, c1, c2;
 };
 
+// one warp per parameter (the last warp also sums the loss): lane l adds partials l, l + 32, ...
+// in order, loading eight at a time, then the lanes' sums meet in a fixed shuffle tree, so the
+// result does not depend on timing
+__device__ __forceinline__ float warp_fixed_sum(const float *v, size_t stride, int n) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.0f;
+    for (int b0 = lane; b0 < n; b0 += 32 * 8) {
+        float t[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int b = b0 + 32 * q;
+            t[q] = b < n ? v[(size_t)b * stride] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (b0 + 32 * q < n) acc = __fadd_rn(acc, t[q]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_down_sync(0xFFFFFFFFu, acc, o));
+    return acc;
+}
+
 __global__ void k_reduce(ReduceArgs r) {
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0 && r.loss_partials && r.loss_out) {
-        float l = 0.0f;
-        for (int b = 0; b < r.blocks; ++b) l = __fadd_rn(l, r.loss_partials[b]);
-        *r.loss_out = l * r.loss_scale;
+    const size_t p = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p == r.P && r.loss_partials && r.loss_out) {
+        const float l = warp_fixed_sum(r.loss_partials, 1, r.blocks);
+        if (lane == 0) *r.loss_out = l * r.loss_scale;
     }
     if (p >= r.P) return;
-    float g = 0.0f;
-    for (int b = 0; b < r.blocks; ++b) g = __fadd_rn(g, r.partials[(size_t)b * r.P + p]);
+    const float g = warp_fixed_sum(r.partials + p, r.P, r.blocks);
+    if (lane != 0) return;
     if (r.out) r.out[p] = g;
     if (r.params) {
         const float m = r.b1 * r.m[p] + (1.0f - r.b1) * g;
@@ -554,7 +576,7 @@ cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, 
     ReduceArgs r{};
     r.partials = partials; r.blocks = blocks; r.P = P; r.out = out;
     r.loss_partials = loss_partials; r.loss_out = loss_out; r.loss_scale = scale;
-    k_reduce<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(r);
+    k_reduce<<<(unsigned)(((P + 1) * 32 + 255) / 256), 256, 0, s>>>(r);
     return nns_launched(cudaGetLastError());
 }
 
@@ -576,7 +598,7 @@ cudaError_t launch_train_step(const PadArch &a, const TrainStepArgs &t, cudaStre
     const double c1 = 1.0 - std::pow((double)t.b1, (double)(t.step + 1));
     const double c2 = 1.0 - std::pow((double)t.b2, (double)(t.step + 1));
     r.c1 = (float)c1; r.c2 = (float)c2;
-    k_reduce<<<(unsigned)((t.P + 255) / 256), 256, 0, s>>>(r);
+    k_reduce<<<(unsigned)(((t.P + 1) * 32 + 255) / 256), 256, 0, s>>>(r);
     return nns_launched(cudaGetLastError());
 }
 

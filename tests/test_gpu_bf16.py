@@ -33,14 +33,22 @@ def _emulate(params: np.ndarray, h: int, x: np.ndarray, split: bool = False):
     b2 = p[2 * h + h * h:3 * h + h * h]
     W3 = p[3 * h + h * h:4 * h + h * h]
     b3 = p[4 * h + h * h]
-    a = orc.mlp_layer1_f32(2, h, h, params, x)  # binary32 first layer
-    h1 = _bf16(a)
-    if split:  # the residual a - bf16(a) is exact in binary32, then rounded to BF16
-        h1 = h1 + _bf16((a.astype(np.float64) - h1).astype(np.float32))
-    z = h1 @ _bf16(W2.astype(np.float32)).T
+    a = orc.mlp_layer1_f32(2, h, h, params, x)  # binary32 first layer (after the ReLU)
+    W2b = _bf16(W2.astype(np.float32))
+    if split:
+        # a = hi + lo: hi = a truncated to BF16 (8 significant bits) times W2 in BF16, plus
+        # lo = the exact binary32 rest rounded to FP16 times W2 in FP16
+        hi = (a.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32).astype(np.float64)
+        lo = (a.astype(np.float64) - hi).astype(np.float32).astype(np.float16).astype(np.float64)
+        W2h = W2.astype(np.float32).astype(np.float16).astype(np.float64)
+        z = hi @ W2b.T + lo @ W2h.T
+        h1 = hi + lo
+    else:
+        h1 = _bf16(a)
+        z = h1 @ W2b.T
     h2 = np.maximum(z + b2, 0)
     terms = np.abs(h2 * W3).sum(axis=1) + abs(b3)
-    return h2 @ W3 + b3, terms, np.abs(h1) @ np.abs(_bf16(W2.astype(np.float32))).T
+    return h2 @ W3 + b3, terms, np.abs(h1) @ np.abs(W2b).T
 
 
 @pytest.mark.parametrize("h", [16, 32, 64])
