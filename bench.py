@@ -35,7 +35,19 @@ TRAIN = dict(translate="ordbits", sample_n=N_KEYS // 100, steps=100, batch=65536
 SORT = dict(m=1.25, eps=3, tau=1024)
 WORKLOAD = ("268,435,456 float32 keys lognormal(0,2) with 5% exact duplicates, keys only; "
             "MLP 1-64-64-1 trained on the device (1% sample, 100 Adam steps, batch 65536, lr 1e-2); "
-            "m=1.25, eps=3, tau=1024")
+            "m=1.25, tau=1024; bucket width, polish blocks per SM and eps from the autotuned table")
+
+# DRAM bytes per key of one launch, from the ncu captures summarised under profiles/ (2^26 keys,
+# same distribution and model recipe; traffic grows in proportion to the keys)
+TRAFFIC_PER_KEY = {
+    ("predict", "bf16x2"): 7.374,   # profiles/k_predict_bf16_split_64M.md
+    ("rounds", None): 6.805,        # profiles/k_rounds_64M.md
+    ("polish", None): 12.647,       # profiles/k_polish_64M.md
+    ("partition", None): 15.943,    # profiles/k_onesweep_partition_64M.md (per pass)
+}
+# binary32 operations per key on the CUDA cores in the tensor-core predict (layer 1: H FMA; split
+# form: H residual subtractions; output layer: H additions and H FMA; FMA = 2)
+CUDA_CORE_FLOP_PER_KEY = {"bf16": 2 * 64 + 64 + 2 * 64, "bf16x2": 2 * 64 + 64 + 64 + 2 * 64}
 
 
 def peaks():
@@ -199,9 +211,9 @@ def serving_leg(nns, W, count=200, rate=400.0, seed=5):
 
 
 # --------------------------------------------------------------------------- GPU arm
-def run_job(nns, keys, precision, sopts, stats=True):
+def run_job(nns, keys, precision, sopts, stats=True, timing=False):
     model, hist = nns.train(keys, **ARCH, **TRAIN)
-    st = nns.sort(keys, None, model, precision=precision, stats=stats, **sopts)
+    st = nns.sort(keys, None, model, precision=precision, stats=stats, timing=timing, **sopts)
     return model, hist, st
 
 
@@ -251,9 +263,8 @@ def main():
     if precision == "auto":
         # the tensor-core form the autotuner measured faster on this workload class
         from paper_1907_08817_gb300 import autotune as AT
-        tbl = AT.load_table()
-        cands = [(tbl[k]["sort_ms"], p) for p in ("bf16x2", "bf16")
-                 if (k := AT.table_key(0, n, ARCH["layers"], ARCH["h1"], ARCH["h2"], p)) in tbl]
+        cands = [(e["sort_ms"], p) for p in ("bf16x2", "bf16")
+                 if (e := AT.tuned_entry(0, n, ARCH["layers"], ARCH["h1"], ARCH["h2"], p)) is not None]
         precision = min(cands)[1] if cands else "bf16"
 
     sopts = tuned_sort_opts(precision, n)
@@ -264,6 +275,7 @@ def main():
     torch.cuda.synchronize()
     # timed region: K whole jobs, each on its own resident input
     launches0 = L.lib().nnsort_launch_count()
+    timed_stages = []
     clk = Clocks(local)
     with clk:
         barrier(ws)
@@ -272,7 +284,9 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s)
         for k in range(args.steps):
-            run_job(nns, bufs[args.warmup + k], precision, sopts, stats=False)
+            # the library records CUDA events around each stage on the call's stream
+            timed_stages.append(run_job(nns, bufs[args.warmup + k], precision, sopts,
+                                        timing=True)[2]["ms_stage"])
         e1.record(s)
         torch.cuda.synchronize()
         barrier(ws)
@@ -343,32 +357,41 @@ def main():
                  "stage_ms": dict(zip(["predict", "partition", "bucket_bounds", "rounds",
                                        "finalize", "polish", "seam"], best["ms_stage"][:7]))}
 
-    # roofline of the dominant kernel stage
+    # roofline of the dominant kernel stage: its mean duration over the timed steps (events the
+    # library records on the call's stream)
     kb = 4
     names = ["predict", "partition", "bucket_bounds", "rounds", "finalize", "polish", "seam"]
-    dom = max(range(7), key=lambda i: stage[i])
+    live = [statistics.mean(r[i] for r in timed_stages) for i in range(8)]
+    dom = max(range(7), key=lambda i: live[i])
     npass = st["partition_passes"]
     alg = {0: n * (kb + 4), 1: npass * n * 2 * (kb + 4), 2: 0, 3: n * (kb + 4 + 1), 4: 0,
            5: n * (2 * kb + 5), 6: 0}
-    dom_ms = stage[dom]
+    dom_ms = live[dom]
+    tpk = TRAFFIC_PER_KEY.get((names[dom], precision), TRAFFIC_PER_KEY.get((names[dom], None)))
+    traffic = None
+    if tpk is not None:
+        traffic = tpk * n * (npass if dom == 1 else 1)
+    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     if dom == 0 and precision in ("bf16", "bf16x2"):
-        flops = n * 2 * 64 * 64 * (2 if precision == "bf16x2" else 1)
-        ach = flops / (dom_ms / 1e3) / 1e12
-        roof = {"kernel": "predict (k_predict_bf16)", "bound": "tensor", "achieved": ach,
-                "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops"],
-                "traffic": None, "peak_source": pk["source"]}
+        # bound by the binary32 work on the CUDA cores around the tensor-core layer
+        ach = n * CUDA_CORE_FLOP_PER_KEY[precision] / (dom_ms / 1e3) / 1e12
+        tens = n * 2 * 64 * 64 * (2 if precision == "bf16x2" else 1) / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": "predict (k_predict_bf16)", "bound": "alu", "achieved": ach,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+                "tensor": {"achieved": tens, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                           "frac": tens / pk["bf16_tflops"], "peak_source": pk["source"]}}
     elif dom == 0:
-        flops = n * 2 * (64 + 64 * 64 + 64)
-        fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-        ach = flops / (dom_ms / 1e3) / 1e12
+        ach = n * 2 * (64 + 64 * 64 + 64) / (dom_ms / 1e3) / 1e12
         roof = {"kernel": "predict (k_predict, binary32 FFMA)", "bound": "alu", "achieved": ach,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
     else:
         ach = alg[dom] / (dom_ms / 1e3) / 1e9
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": traffic,
                 "peak_source": pk["source"]}
+    roof["ms"] = dom_ms
     # the whole sort against the path's algorithmic bytes (4 passes + 3 per re-mapped conflict)
     w = st["w_size"]
     b_alg = 4 * n * kb + 3 * sum(w[1:-1]) * kb if len(w) > 2 else 4 * n * kb

@@ -97,22 +97,28 @@ def save_entry(key: str, cfg: dict, ms: float, path: str = TABLE) -> None:
     _cache.pop(path, None)
 
 
+def tuned_entry(dtype: int, n: int, layers: int, h1: int, h2: int, precision: str,
+                path: str = TABLE) -> dict | None:
+    """The table entry for this workload class: n's size class, else the nearest tuned size class
+    of the same key type, model shape and precision, else None."""
+    t = load_table(path)
+    key = table_key(dtype, n, layers, h1, h2, precision)
+    if key in t:
+        return t[key]
+    prefix = f"d{dtype}-"
+    suffix = key.split("-", 2)[2]
+    cands = [(abs(int(k.split("-")[1][1:]) - int(math.log2(max(n, 1)))), k) for k in t
+             if k.startswith(prefix) and k.split("-", 2)[2] == suffix]
+    return t[min(cands)[1]] if cands else None
+
+
 def tuned_options(dtype: int, n: int, layers: int, h1: int, h2: int, precision: str,
                   path: str = TABLE) -> dict:
     """Tuned keyword arguments for sort()/sort_batch(); the nearest table entry of the same key
     type, model shape and precision when n's class was not tuned, else the library defaults."""
-    t = load_table(path)
-    key = table_key(dtype, n, layers, h1, h2, precision)
-    if key in t:
-        e = t[key]
-    else:
-        prefix = f"d{dtype}-"
-        suffix = key.split("-", 2)[2]
-        cands = [(abs(int(k.split("-")[1][1:]) - int(math.log2(max(n, 1)))), k) for k in t
-                 if k.startswith(prefix) and k.split("-", 2)[2] == suffix]
-        if not cands:
-            return dict(DEFAULTS)
-        e = t[min(cands)[1]]
+    e = tuned_entry(dtype, n, layers, h1, h2, precision, path)
+    if e is None:
+        return dict(DEFAULTS)
     return {k: e[k] for k in DEFAULTS if k in e}
 
 

@@ -18,8 +18,8 @@ struct OKey;
 constexpr int RADIX_MAX_BITS = 9;
 constexpr int RADIX_BINS = 1 << RADIX_MAX_BITS;  // 512
 constexpr int PART_THREADS = 512;
-constexpr int PART_ITEMS = 8;
-constexpr int PART_TILE = PART_THREADS * PART_ITEMS;  // 4096
+constexpr int PART_ITEMS = 16;
+constexpr int PART_TILE = PART_THREADS * PART_ITEMS;  // 8192
 constexpr int PRED_THREADS = 256;
 constexpr int PRED_ITEMS = 8;
 constexpr int PRED_TILE = PRED_THREADS * PRED_ITEMS;  // 2048

@@ -43,7 +43,7 @@ struct PartSmem {
 }  // namespace
 
 template <typename W, bool KEYDIG, bool PAY, bool ROW>
-__global__ void __launch_bounds__(PART_THREADS, 2) k_onesweep(OnesweepArgs a) {
+__global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     PartSmem &S = *reinterpret_cast<PartSmem *>(smraw);
     __shared__ uint32_t lstart[RADIX_BINS];
