@@ -43,7 +43,7 @@ TRAFFIC_PER_KEY = {
     ("predict", "bf16x2"): 7.374,   # profiles/k_predict_bf16_split_64M.md
     ("rounds", None): 6.805,        # profiles/k_rounds_64M.md
     ("polish", None): 12.647,       # profiles/k_polish_64M.md
-    ("partition", None): 15.943,    # profiles/k_onesweep_partition_64M.md (per pass)
+    ("partition", None): 15.560,    # profiles/k_onesweep_partition_64M.md (per pass)
 }
 # binary32 operations per key on the CUDA cores in the tensor-core predict (layer 1: H FMA; split
 # form: H residual subtractions; output layer: H additions and H FMA; FMA = 2)
@@ -351,11 +351,51 @@ def main():
             runs.append(nns.sort(job, None, model, precision=op_, timing=True, **oo))
         best = min(runs, key=lambda r: r["ms_stage"][7])
         other = {"precision": op_, "sort_opts": oo, "sort_ms": best["ms_stage"][7],
-                 "sigma": best["sigma"], "repaired": best["repaired"],
+                 "sigma": best["sigma"], "w_size": best["w_size"], "repaired": best["repaired"],
                  "repair_ranges": best["repair_ranges"],
                  "oversized_buckets": best["oversized_buckets"],
                  "stage_ms": dict(zip(["predict", "partition", "bucket_bounds", "rounds",
                                        "finalize", "polish", "seam"], best["ms_stage"][:7]))}
+
+    # the compiled form of the same model: its piecewise-linear form evaluated per key by one binary
+    # search and one multiply-add (the binary64 model's positions)
+    compiled = None
+    slot_error = None
+    if not args.no_plain and precision != "pwl":
+        po = tuned_sort_opts("pwl", n)
+        runs = []
+        for _ in range(2):
+            job.copy_(pristine)
+            torch.cuda.synchronize()
+            runs.append(nns.sort(job, None, model, precision="pwl", timing=True, **po))
+        best = min(runs, key=lambda r: r["ms_stage"][7])
+        compiled = {"precision": "pwl", "sort_opts": po, "sort_ms": best["ms_stage"][7],
+                    "job_ms": train_ms + best["ms_stage"][7],
+                    "value": n / ((train_ms + best["ms_stage"][7]) / 1e3) / 1e6,
+                    "sigma": best["sigma"], "repaired": best["repaired"],
+                    "repair_ranges": best["repair_ranges"],
+                    "oversized_buckets": best["oversized_buckets"],
+                    "stage_ms": dict(zip(["predict", "partition", "bucket_bounds", "rounds",
+                                          "finalize", "polish", "seam"], best["ms_stage"][:7]))}
+        # slot displacement of each form against the binary64 model's positions, and the share of
+        # keys that conflict in the first mapping round of its sort
+        w1 = {precision: st["w_size"], "pwl": best["w_size"]}
+        if plain is not None:
+            w1["fp32"] = st_p["w_size"]
+        if other is not None:
+            w1[other["precision"]] = other["w_size"]
+        ref, _ = nns.predict(pristine, model, precision="pwl", want_y=False)
+        slot_error = {"against": "positions of the binary64 model (its compiled form)"}
+        for p_ in ("bf16x2", "bf16", "fp32"):
+            sp, _ = nns.predict(pristine, model, precision=p_, want_y=False)
+            d = (sp - ref).abs_()
+            slot_error[p_] = {"mean_abs": float(d.double().mean()), "max_abs": int(d.max()),
+                              "frac_moved": float((d != 0).double().mean()),
+                              "conflict_rate": (w1[p_][1] / n if p_ in w1 and len(w1[p_]) > 1
+                                                else None)}
+            del sp, d
+        slot_error["pwl"] = {"conflict_rate": w1["pwl"][1] / n if len(w1["pwl"]) > 1 else None}
+        del ref
 
     # roofline of the dominant kernel stage: its mean duration over the timed steps (events the
     # library records on the call's stream)
@@ -381,7 +421,7 @@ def main():
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
                 "tensor": {"achieved": tens, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                            "frac": tens / pk["bf16_tflops"], "peak_source": pk["source"]}}
-    elif dom == 0:
+    elif dom == 0 and precision == "fp32":
         ach = n * 2 * (64 + 64 * 64 + 64) / (dom_ms / 1e3) / 1e12
         roof = {"kernel": "predict (k_predict, binary32 FFMA)", "bound": "alu", "achieved": ach,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
@@ -450,7 +490,8 @@ def main():
                           "oversized_buckets": st["oversized_buckets"], "repaired": st["repaired"],
                           "repair_ranges": st["repair_ranges"],
                           "final_train_loss": float(hist[-1])},
-                "plain": plain, "other_tensor_form": other, "serving": serving, "cpu_baseline": cpu, "e2e": e2e,
+                "plain": plain, "other_tensor_form": other, "compiled_form": compiled,
+                "slot_error": slot_error, "serving": serving, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(),
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)

@@ -68,7 +68,18 @@ typedef enum { NNSORT_TRANSLATE_ORDBITS = 0, NNSORT_TRANSLATE_VALUE = 1 } nnsort
  * (two MMA chains): the activations keep ~19 significant bits, so F stays about as finely resolved
  * in x as the binary32 model (the weights' rounding only changes f smoothly). Two-hidden-layer
  * models only; others use binary32. */
-typedef enum { NNSORT_PREC_FP32 = 0, NNSORT_PREC_BF16 = 1, NNSORT_PREC_BF16X2 = 2 } nnsort_precision;
+typedef enum {
+    NNSORT_PREC_FP32 = 0,
+    NNSORT_PREC_BF16 = 1,
+    NNSORT_PREC_BF16X2 = 2,
+    /* PWL: f compiled into its piecewise-linear form (a 1-D ReLU MLP is piecewise linear in x) in
+     * binary64 on the host, then per key one binary search over the segments' order-image
+     * thresholds and one multiply-add in pairs of binary32 (~48 significant bits; binary64 only to
+     * normalise f64 keys): the positions of the binary64 model up to rounding, and no binary32
+     * resolution limit in translate or the forward pass. Single-array sorts and nnsort_predict only (a batch
+     * returns NNSORT_E_UNSUPPORTED). */
+    NNSORT_PREC_PWL = 3
+} nnsort_precision;
 
 /* Training loss: mean squared error, or the Huber loss of Eq. (loss). */
 typedef enum { NNSORT_LOSS_MSE = 0, NNSORT_LOSS_HUBER = 1 } nnsort_loss;
@@ -184,6 +195,17 @@ int nnsort_model_describe(const nnsort_model *f, nnsort_model_desc *desc, float 
 size_t nnsort_model_blob_size(const nnsort_model *f);
 int nnsort_model_save(const nnsort_model *f, void *h_blob, size_t cap);
 int nnsort_model_load(const void *h_blob, size_t size, nnsort_model **out);
+
+/* The piecewise-linear form of the model f with parameters h_params (binary32, the layout of
+ * nnsort_model_create, host memory): a ReLU MLP of one input is piecewise linear (the map line of
+ * Fig. "Algorithm NN-sort"). Computed on the host in binary64: segment i covers translated inputs
+ * x in [h_breaks[i], h_breaks[i+1]) (h_breaks[0] = -infinity, the last segment is unbounded) and
+ * there F(x) = h_slope[i] * x + h_icept[i]. Host arrays of `cap` entries, written in increasing x;
+ * *count receives the number of segments (at most h1 + 1 for one hidden layer, 1 + h1 + (h1 + 1) h2
+ * for two). Returns NNSORT_E_INVALID_ARG, with *count set, when cap is too small. No device work;
+ * usable without a GPU. NNSORT_PREC_PWL sorts use this form. */
+int nnsort_mlp_pwl(int32_t layers, int32_t h1, int32_t h2, const float *h_params, double *h_breaks,
+                   double *h_slope, double *h_icept, uint32_t cap, uint32_t *count);
 
 /* ---- training (Sec. "Training", Eq. (loss)) ------------------------------------------- */
 /* Training data: S keys drawn with replacement (draw j picks row floor(u_j n / 2^64) with u_j

@@ -62,7 +62,7 @@ def _ptr(t):
 def _prec(p) -> int:
     if isinstance(p, int):
         return p
-    return {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16x2": L.PREC_BF16X2}[p]
+    return {"fp32": PREC_FP32, "bf16": PREC_BF16, "bf16x2": L.PREC_BF16X2, "pwl": L.PREC_PWL}[p]
 
 
 def _tr(t) -> int:
@@ -121,6 +121,11 @@ class Model:
             self._h, None, p.ctypes.data_as(C.c_void_p)))
         return {"dtype": d.dtype, "translate": d.translate, "layers": d.layers, "h1": d.h1,
                 "h2": d.h2, "lo_bits": d.lo_bits, "lo_val": d.lo_val, "scale": d.scale}, p
+
+    def pwl(self):
+        """The piecewise-linear form of f: see mlp_pwl."""
+        d, p = self.describe()
+        return mlp_pwl(p, d["layers"], d["h1"], d["h2"])
 
     def save(self) -> bytes:
         n = L.lib().nnsort_model_blob_size(self._h)
@@ -284,6 +289,22 @@ def sort_batch(keys_list, models, payloads=None, *, m=1.25, eps=3, tau=1024, pre
 
 def workspace_bytes(n: int, dtype: int, with_payload: bool = False) -> int:
     return int(L.lib().nnsort_workspace_bytes(n, dtype, int(with_payload), None))
+
+
+def mlp_pwl(params, layers, h1, h2=0):
+    """Piecewise-linear form of the MLP (nnsort_mlp_pwl, host only): (breaks, slope, icept) float64
+    arrays, segment i covering translated inputs [breaks[i], breaks[i+1]) with F = slope[i] x +
+    icept[i] (breaks[0] = -inf)."""
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    cnt = C.c_uint32()
+    lib = L.lib()
+    lib.nnsort_mlp_pwl(layers, h1, h2, p.ctypes.data_as(C.c_void_p), None, None, None, 0, C.byref(cnt))
+    n = cnt.value
+    b, sl, ic = (np.empty(n, np.float64) for _ in range(3))
+    L.check("nnsort_mlp_pwl", lib.nnsort_mlp_pwl(
+        layers, h1, h2, p.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p),
+        sl.ctypes.data_as(C.c_void_p), ic.ctypes.data_as(C.c_void_p), n, C.byref(cnt)))
+    return b, sl, ic
 
 
 # ------------------------------------------------------------------- forward / backward

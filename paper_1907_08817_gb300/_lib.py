@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libnnsort.so")
 MAX_ROUNDS = 8
 F32, F64, U32, U64 = 0, 1, 2, 3
 ORDBITS, VALUE = 0, 1
-PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_BF16X2, PREC_PWL = 0, 1, 2, 3
 LOSS_MSE, LOSS_HUBER = 0, 1
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "NaN key", -3: "out of memory",
@@ -102,6 +102,7 @@ def lib():
         "nnsort_model_blob_size": (sz, [P]),
         "nnsort_model_save": (C.c_int, [P, P, sz]),
         "nnsort_model_load": (C.c_int, [P, sz, P]),
+        "nnsort_mlp_pwl": (C.c_int, [i32, i32, i32, P, P, P, P, C.c_uint32, P]),
         "nnsort_sample_labels": (C.c_int, [P, u64, i32, u64, u64, i32, P, P, P, P, P]),
         "nnsort_train": (C.c_int, [P, u64, i32, P, P, P, P]),
         "nnsort_mlp_forward": (C.c_int, [P, i32, i32, i32, P, u64, P, P]),
@@ -134,7 +135,8 @@ def exported_symbols() -> list[str]:
             "nnsort_default_train_opts", "nnsort_default_sort_opts", "nnsort_release",
             "nnsort_stream_status", "nnsort_workspace_bytes", "nnsort_model_create",
             "nnsort_model_free", "nnsort_model_describe", "nnsort_model_blob_size",
-            "nnsort_model_save", "nnsort_model_load", "nnsort_sample_labels", "nnsort_train",
+            "nnsort_model_save", "nnsort_model_load", "nnsort_mlp_pwl", "nnsort_sample_labels",
+            "nnsort_train",
             "nnsort_mlp_forward", "nnsort_mlp_backward", "nnsort_mlp_loss_grad",
             "nnsort_predict", "nnsort_sort", "nnsort_sort_host", "nnsort_sort_batch",
             "nnsort_train_sort_host", "nnsort_launch_count", "nnsort_sort_noalloc",

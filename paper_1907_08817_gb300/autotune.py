@@ -223,6 +223,7 @@ def _main(argv: Iterable[str]) -> None:
         ("lognormal_dup_f32 256M 1-64-64-1", big, "bf16x2"),
         ("lognormal_dup_f32 256M 1-64-64-1", big, "bf16"),
         ("lognormal_dup_f32 256M 1-64-64-1", big, "fp32"),
+        ("lognormal_dup_f32 256M 1-64-64-1", big, "pwl"),
         ("uniform_f32 1M 1-32-1", one(lambda n: W.uniform_f32(n, 0), 1_000_000, (1, 32, 0)), "fp32"),
         ("gauss_mix_u64 64M + payload 1-32-1", one(lambda n: W.gauss_mix_u64(n, 3), 1 << 26,
                                                    (1, 32, 0), steps=200), "fp32"),

@@ -376,6 +376,19 @@ int nnsort_model_describe(const nnsort_model *f, nnsort_model_desc *desc, float 
     return NNSORT_OK;
 }
 
+int nnsort_mlp_pwl(int32_t layers, int32_t h1, int32_t h2, const float *h_params, double *h_breaks,
+                   double *h_slope, double *h_icept, uint32_t cap, uint32_t *count) {
+    if (!count || !h_params || !arch_ok(layers, h1, h2)) return NNSORT_E_INVALID_ARG;
+    std::vector<double> brk, slope, icept;
+    pwl_segments(layers, h1, layers == 1 ? 0 : h2, h_params, brk, slope, icept);
+    *count = (uint32_t)brk.size();
+    if (cap < brk.size() || !h_breaks || !h_slope || !h_icept) return NNSORT_E_INVALID_ARG;
+    std::memcpy(h_breaks, brk.data(), brk.size() * sizeof(double));
+    std::memcpy(h_slope, slope.data(), slope.size() * sizeof(double));
+    std::memcpy(h_icept, icept.data(), icept.size() * sizeof(double));
+    return NNSORT_OK;
+}
+
 static const uint32_t BLOB_MAGIC = 0x4E4E5331u;  // "NNS1"
 size_t nnsort_model_blob_size(const nnsort_model *f) {
     return f ? 8 + sizeof(nnsort_model_desc) + f->P * sizeof(float) : 0;
@@ -725,7 +738,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     if (op) o = *op; else nnsort_default_sort_opts(&o);
     if (!dtype_ok(dtype)) return NNSORT_E_INVALID_ARG;
     if (!(o.m > 0.0f) || o.eps < 0 || o.eps > NNSORT_MAX_ROUNDS) return NNSORT_E_INVALID_ARG;
-    if (o.precision < NNSORT_PREC_FP32 || o.precision > NNSORT_PREC_BF16X2) return NNSORT_E_INVALID_ARG;
+    if (o.precision < NNSORT_PREC_FP32 || o.precision > NNSORT_PREC_PWL) return NNSORT_E_INVALID_ARG;
     if (in.size() > 1 && (o.d_slots || o.d_fate)) return NNSORT_E_INVALID_ARG;
     const nnsort_model *f0 = nullptr;
     bool anypay = false;
@@ -748,11 +761,20 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     if (P.N == 0) return NNSORT_OK;
     const int kb = key_bytes_of(dtype);
     const bool rows = o.d_fate != nullptr || (o.d_slots != nullptr && anypay);
+    // the compiled piecewise-linear form of f: computed here on the host, staged after the layout
+    const bool pwl = f0 && !o.d_slots && o.precision == NNSORT_PREC_PWL;
+    std::vector<double> pbrk, pslope, picept;
+    if (pwl) {
+        if (nseg != 1) return NNSORT_E_UNSUPPORTED;
+        pwl_segments(f0->desc.layers, f0->desc.h1, f0->desc.h2, f0->params.data(), pbrk, pslope, picept);
+    }
+    const size_t pwl_bytes = pbrk.size() * sizeof(PwlEntry);
     size_t need = 0;
     carve(nullptr, nseg, P.N, P.NB, kb, anypay, rows, &need);
+    const size_t pwl_off = align_up(need, 256);
     Workspace *w = nullptr;
     if ((rc = get_ws(s, &w))) return rc;
-    if ((rc = ensure_arena(w, need, s))) return rc;
+    if ((rc = ensure_arena(w, pwl_off + pwl_bytes, s))) return rc;
     const uint64_t ptiles = (P.N + PART_TILE - 1) / PART_TILE;
     if ((rc = ensure_lookback(w, ptiles * RADIX_BINS, s))) return rc;
     // staging: the segment table, then the statistics, the seam counters and the long seam ranges
@@ -762,7 +784,8 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     const size_t pin_rng = pin_cnt + 64;
     const size_t pin_hist = align_up(pin_rng + sizeof(SeamRange) * (P.N / SEAM_CTA_MAX + 1), 64);
     const size_t pin_big = align_up(pin_hist + sizeof(uint32_t) * 4 * RADIX_BINS, 64);
-    const size_t pin_need = pin_big + sizeof(BigRange) * (P.N / POLISH_BIG + 1) + 256;
+    const size_t pin_pwl = align_up(pin_big + sizeof(BigRange) * (P.N / POLISH_BIG + 1), 64);
+    const size_t pin_need = pin_pwl + pwl_bytes + 256;
     if ((rc = ensure_pinned(w, pin_need, s))) return rc;
     size_t total = 0;
     Layout L = carve(w->arena, nseg, P.N, P.NB, kb, anypay, rows, &total);
@@ -773,6 +796,15 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     CK(cudaStreamSynchronize(s));
     std::memcpy(w->pinned, P.segs.data(), sizeof(Seg) * nseg);
     CK(cudaMemcpyAsync(L.segs, w->pinned, sizeof(Seg) * nseg, cudaMemcpyHostToDevice, s));
+    PwlDev pwl_dev{};
+    if (pwl) {
+        PwlEntry *hp = reinterpret_cast<PwlEntry *>(w->pinned + pin_pwl);
+        pwl_key_table(f0->desc, pbrk, pslope, picept, (double)P.segs[0].nm_hi + (double)P.segs[0].nm_lo, hp);
+        PwlEntry *dp = reinterpret_cast<PwlEntry *>(w->arena + pwl_off);
+        CK(cudaMemcpyAsync(dp, hp, pwl_bytes, cudaMemcpyHostToDevice, s));
+        pwl_dev.tab = dp;
+        pwl_dev.S = (uint32_t)pbrk.size();
+    }
     CK(cudaMemsetAsync(L.stats, 0, sizeof(SegStats) * nseg, s));
     CK(cudaMemsetAsync(L.err, 0, 16, s));
     CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * MAX_PASSES * RADIX_BINS, s));
@@ -797,6 +829,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     pa.err = L.err;
     pa.key_bytes = kb;
     pa.dtype = dtype;
+    pa.pwl = pwl_dev;
     const PadArch arch = f0 ? f0->pad : pad_arch(1, 8, 0);
     const int prec = f0 ? o.precision : NNSORT_PREC_FP32;
     {
@@ -1083,7 +1116,7 @@ int nnsort_sort_host(void *h_keys, int32_t *h_payload, uint64_t n, int32_t dtype
 int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_model *f, float m,
                    int32_t precision, uint32_t *d_slots, float *d_y, cudaStream_t stream) {
     if (!f || !dtype_ok(dtype) || f->desc.dtype != dtype || !(m > 0.0f)) return NNSORT_E_INVALID_ARG;
-    if (precision < NNSORT_PREC_FP32 || precision > NNSORT_PREC_BF16X2) return NNSORT_E_INVALID_ARG;
+    if (precision < NNSORT_PREC_FP32 || precision > NNSORT_PREC_PWL) return NNSORT_E_INVALID_ARG;
     if (n && !d_keys) return NNSORT_E_INVALID_ARG;
     if (n >= 0xFFFFFFFFull || (double)n * m >= 4294967295.0) return NNSORT_E_INVALID_ARG;
     if (n == 0) return NNSORT_OK;
@@ -1095,16 +1128,30 @@ int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_m
     Plan P;
     int rc = make_plan(in, o, dtype, P);
     if (rc) return rc;
+    std::vector<double> pbrk, pslope, picept;
+    if (precision == NNSORT_PREC_PWL)
+        pwl_segments(f->desc.layers, f->desc.h1, f->desc.h2, f->params.data(), pbrk, pslope, picept);
+    const size_t pwl_bytes = pbrk.size() * sizeof(PwlEntry);
     Workspace *w = nullptr;
     if ((rc = get_ws(stream, &w))) return rc;
-    if ((rc = ensure_arena(w, 4096, stream))) return rc;
-    if ((rc = ensure_pinned(w, sizeof(Seg) + 64, stream))) return rc;
+    if ((rc = ensure_arena(w, 4096 + pwl_bytes, stream))) return rc;
+    if ((rc = ensure_pinned(w, 256 + pwl_bytes, stream))) return rc;
+    static_assert(sizeof(Seg) <= 256, "the staged segment fits before the compiled table");
     Seg *dseg = reinterpret_cast<Seg *>(w->arena);
     uint32_t *err = reinterpret_cast<uint32_t *>(w->arena + 2048);
     CK(cudaStreamSynchronize(stream));
     std::memcpy(w->pinned, &P.segs[0], sizeof(Seg));
     CK(cudaMemcpyAsync(dseg, w->pinned, sizeof(Seg), cudaMemcpyHostToDevice, stream));
     CK(cudaMemsetAsync(err, 0, 4, stream));
+    PwlDev pwl_dev{};
+    if (!pbrk.empty()) {
+        PwlEntry *hp = reinterpret_cast<PwlEntry *>(w->pinned + 256);
+        pwl_key_table(f->desc, pbrk, pslope, picept, (double)P.segs[0].nm_hi + (double)P.segs[0].nm_lo, hp);
+        PwlEntry *dp = reinterpret_cast<PwlEntry *>(w->arena + 4096);
+        CK(cudaMemcpyAsync(dp, hp, pwl_bytes, cudaMemcpyHostToDevice, stream));
+        pwl_dev.tab = dp;
+        pwl_dev.S = (uint32_t)pbrk.size();
+    }
     PredictArgs pa{};
     pa.segs = dseg;
     pa.nseg = 1;
@@ -1115,6 +1162,7 @@ int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_m
     pa.err = err;
     pa.key_bytes = key_bytes_of(dtype);
     pa.dtype = dtype;
+    pa.pwl = pwl_dev;
     w->last_err = err;
     cudaError_t e = launch_predict(f->pad, precision, pa, sm_count(), stream);
     if (e == cudaErrorNotSupported) return NNSORT_E_UNSUPPORTED;

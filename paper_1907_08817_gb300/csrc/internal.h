@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "nnsort.h"
@@ -43,6 +44,17 @@ size_t padded_param_count(const PadArch &a);
 // Fills gs (global position per element), optional key / payload / row copies into the element
 // space and the per-pass digit histograms hist[npass][RADIX_BINS]. Also serves nnsort_predict
 // through slots_out / y_out (element space of a single array).
+// one segment of the compiled piecewise-linear model in the keys' order-image domain (pwl.cu)
+struct PwlEntry {
+    unsigned long long thr;  // smallest order image in the segment (0 for the first)
+    float Ah, Al, Ch, Cl;    // position = floor(A d + C), d = translate offset of the key, with
+                             // A = Ah + Al and C = Ch + Cl (pairs of binary32: ~48 significant bits)
+};
+struct PwlDev {
+    const PwlEntry *tab;     // device table, null when the compiled form is not used
+    uint32_t S;              // segments
+};
+
 struct PredictArgs {
     const Seg *segs;
     int nseg;
@@ -58,9 +70,17 @@ struct PredictArgs {
     uint32_t *err;
     int key_bytes;
     int dtype;
+    PwlDev pwl;              // NNSORT_PREC_PWL (single array)
 };
 cudaError_t launch_predict(const PadArch &a, int precision, const PredictArgs &p, int sms,
                            cudaStream_t s);
+cudaError_t launch_predict_pwl(const PredictArgs &p, int sms, cudaStream_t s);
+// host side of the compiled form (pwl.cu)
+void pwl_segments(int layers, int h1, int h2, const float *params, std::vector<double> &brk,
+                  std::vector<double> &slope, std::vector<double> &icept);
+uint32_t pwl_max_segments(int layers, int h1, int h2);
+void pwl_key_table(const nnsort_model_desc &d, const std::vector<double> &brk, const std::vector<double> &slope,
+                   const std::vector<double> &icept, double nm, PwlEntry *out);
 
 // ---- partition (k_partition.cu)
 struct OnesweepArgs {

@@ -106,6 +106,7 @@ cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, bool spl
 
 cudaError_t launch_predict(const PadArch &a, int precision, const PredictArgs &p, int sms,
                            cudaStream_t s) {
+    if (precision == NNSORT_PREC_PWL) return launch_predict_pwl(p, sms, s);
     if ((precision == NNSORT_PREC_BF16 || precision == NNSORT_PREC_BF16X2) && a.layers == 2)
         return launch_predict_bf16(a, p, precision == NNSORT_PREC_BF16X2, sms, s);
     if (a.layers == 1) {
