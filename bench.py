@@ -12,6 +12,7 @@ the plain binary32 form, the roofline of the dominant kernel, an end-to-end figu
 host-array C entry point and the CPU oracle on a bounded sample are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --experiment shift|quickdraw|eps   (the paper's Exp-3, Exp-2 stand-in, Exp-4)
 """
 from __future__ import annotations
 
@@ -210,6 +211,157 @@ def serving_leg(nns, W, count=200, rate=400.0, seed=5):
     return out
 
 
+# --------------------------------------------------------------------------- experiments
+# Sec. "Experimental Study" beside the headline job: each prints one JSON line per setting.
+PAPER_RECIPE = dict(layers=2, h1=2, h2=6, loss="huber", huber_delta=0.01, batch=128, lr=1e-3,
+                    steps=2000)  # three hidden layers of 2, 6 and 1 neurons, Eq. (loss), batch 128
+
+
+def _sorted_ms(nns, torch, src, model, precision, reps=3, **sopts):
+    """Median sort time (the library's stage events), the last run's statistics, and whether the
+    output equals torch.sort of the input."""
+    work = torch.empty_like(src)
+    ms, st = [], None
+    for _ in range(reps):
+        work.copy_(src)
+        torch.cuda.synchronize()
+        st = nns.sort(work, None, model, precision=precision, timing=True, **sopts)
+        ms.append(st["ms_stage"][7])
+    return statistics.median(ms), st, work
+
+
+def _library_sort_ms(torch, src, reps=3):
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        a.record(s)
+        out = torch.sort(src).values
+        b.record(s)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms), out
+
+
+def _host_sort_rate(keys, cap=4_000_000):
+    sample = np.array(keys[:cap])
+    t0 = time.perf_counter()
+    np.sort(sample, kind="quicksort")
+    return sample.shape[0] / (time.perf_counter() - t0) / 1e6
+
+
+def _form(n, ms, st):
+    return {"sort_ms": ms, "mkeys_s": n / (ms / 1e3) / 1e6, "rounds": st["t"],
+            "sigma": st["sigma"], "trad_rate": st["trad_rate"], "repaired": st["repaired"]}
+
+
+def experiment_shift(nns, W, torch):
+    """Exp-3: f (1-32-1, 1% sample, 100 Adam steps, lr 1e-2) trained once on 26,214,400 uniform
+    float32 keys (100 MB), then used unchanged to sort inputs of the same size with 0..60% of the
+    keys replaced by normal(0.5, 0.1) noise; torch.sort (the library's radix sort) and numpy's sort
+    on one host core beside it."""
+    from paper_1907_08817_gb300 import autotune as AT
+    n = 26_214_400
+    tk = torch.from_numpy(W.uniform_f32(n, 0)).cuda()
+    model, _ = nns.train(tk, layers=1, h1=32, h2=0, sample_n=n // 100, steps=100, batch=0, lr=1e-2,
+                         seed=0)
+    del tk
+    for noise in (0.0, 0.15, 0.30, 0.45, 0.60):
+        host = W.shift_mix_f32(n, noise, seed=6)
+        src = torch.from_numpy(host).cuda()
+        lib_ms, ref = _library_sort_ms(torch, src)
+        forms = {}
+        for prec in ("fp32", "pwl"):
+            o = AT.tuned_options(0, n, 1, 32, 0, prec)
+            ms, st, out = _sorted_ms(nns, torch, src, model, prec, **o)
+            assert torch.equal(out, ref), "sorted output differs from torch.sort"
+            forms[prec] = _form(n, ms, st)
+        print(json.dumps({"experiment": "distribution shift (Exp-3)", "n": n, "noise": noise,
+                          "model": "1-32-1 trained on uniform keys", "nnsort": forms,
+                          "torch_sort_ms": lib_ms, "torch_sort_mkeys_s": n / (lib_ms / 1e3) / 1e6,
+                          "host_numpy_sort_mkeys_s": _host_sort_rate(host)}), flush=True)
+        del src, ref
+
+
+def experiment_quickdraw(nns, W, torch):
+    """Exp-2's size: 50,426,265 uniform uint64 keys stand in for the QuickDraw key-ids (not
+    available here); f 1-32-1 trained on a 1% sample of them (100 Adam steps, lr 1e-2)."""
+    from paper_1907_08817_gb300 import autotune as AT
+    n = W.QUICKDRAW_RECORDS
+    host = W.uniform_u64(n, seed=7)
+    src = torch.from_numpy(host.view(np.int64)).cuda()
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    model, _ = nns.train(src, key_type="u64", layers=1, h1=32, h2=0, sample_n=n // 100, steps=100,
+                         batch=0, lr=1e-2, seed=0)
+    b.record(s)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b)
+    flip = torch.tensor(-(1 << 63), dtype=torch.int64, device=src.device)
+    lib_ms, ref = _library_sort_ms(torch, src ^ flip)  # unsigned order as signed
+    forms = {}
+    for prec in ("fp32", "pwl"):
+        o = AT.tuned_options(3, n, 1, 32, 0, prec)
+        work = torch.empty_like(src)
+        ms = []
+        for _ in range(3):
+            work.copy_(src)
+            torch.cuda.synchronize()
+            st = nns.sort(work, None, model, precision=prec, timing=True, key_type="u64", **o)
+            ms.append(st["ms_stage"][7])
+        assert torch.equal(work ^ flip, ref), "sorted output differs from torch.sort"
+        f = _form(n, statistics.median(ms), st)
+        f["job_mkeys_s"] = n / ((train_ms + f["sort_ms"]) / 1e3) / 1e6
+        forms[prec] = f
+    print(json.dumps({"experiment": "QuickDraw-sized stand-in (Exp-2)", "n": n,
+                      "keys": "uint64 uniform over [0, 2^64)", "train_ms": train_ms,
+                      "nnsort": forms, "torch_sort_ms": lib_ms,
+                      "torch_sort_mkeys_s": n / (lib_ms / 1e3) / 1e6,
+                      "host_numpy_sort_mkeys_s": _host_sort_rate(host)}), flush=True)
+
+
+def experiment_eps(nns, W, torch, n, precision):
+    """Exp-4 with the cost model: the headline input sorted with eps = 1..5 under two models (the
+    paper's recipe and the headline one); per eps the sort time, the measured counts (elements
+    entering each iteration, the final conflict array, out-of-order elements) and the cost model's
+    T(n, e, sigma, t, theta) and counts from the measured sigma_i, e_i."""
+    from paper_1907_08817_gb300 import autotune as AT
+    from paper_1907_08817_gb300 import costmodel as CM
+    src = torch.from_numpy(W.lognormal_dup_f32(n, seed=2, sigma=2.0)).cuda()
+    ref = torch.sort(src).values
+    for label, arch, rec, prec in (("paper recipe 1-2-6-1", (2, 2, 6), PAPER_RECIPE, "fp32"),
+                                   ("headline 1-64-64-1", (2, 64, 64),
+                                    dict(**ARCH, **{k: v for k, v in TRAIN.items()
+                                                    if k not in ("translate", "seed")}), precision)):
+        rec = {**rec, "sample_n": max(1, n // 100)}
+        model, hist = nns.train(src, seed=0, **rec)
+        o = AT.tuned_options(0, n, *arch, prec)
+        theta = 2 * (arch[1] + arch[1] * arch[2] + arch[2]) if arch[0] == 2 else 4 * arch[1]
+        for eps in (1, 2, 3, 4, 5):
+            ms, st, out = _sorted_ms(nns, torch, src, model, prec, eps=eps,
+                                     bucket_log2=o["bucket_log2"], polish_blocks=o["polish_blocks"])
+            assert torch.equal(out, ref), "sorted output differs from torch.sort"
+            t = st["t"]
+            w = st["w_size"]
+            sig = [w[i + 1] / w[i] for i in range(t)]
+            e = list(st["e"][:t])
+            pc = CM.predicted_counts(n, sig, e)
+            print(json.dumps({
+                "experiment": "iterations and cost model (Exp-4)", "model": label,
+                "final_train_loss": float(hist[-1]), "precision": prec, "n": n, "eps": eps,
+                "sort_ms": ms, "mkeys_s": n / (ms / 1e3) / 1e6, "t": t,
+                "measured": {"entering": w[:t], "leftover": w[t],
+                             "out_of_order": st["out_of_order"][:t], "sigma": sig, "e": e},
+                "cost_model": {"theta": theta, "entering": pc["entering"],
+                               "leftover": pc["leftover"], "out_of_order": pc["out_of_order"],
+                               "T_printed": CM.operations(n, sig, e, theta, "printed"),
+                               "T_entering": CM.operations(n, sig, e, theta, "entering"),
+                               "n_log2_n": CM.quicksort_operations(n)}}), flush=True)
+        del model
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_job(nns, keys, precision, sopts, stats=True, timing=False):
     model, hist = nns.train(keys, **ARCH, **TRAIN)
@@ -236,6 +388,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--experiment", choices=["shift", "quickdraw", "eps"], default=None,
+                    help="run one of the paper's experiments instead of the benchmark job")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -251,6 +405,16 @@ def main():
     n = args.n
     if args.n != N_KEYS:
         TRAIN["sample_n"] = max(1, n // 100)
+    if args.experiment is not None:
+        if rank == 0:
+            if args.experiment == "shift":
+                experiment_shift(nns, W, torch)
+            elif args.experiment == "quickdraw":
+                experiment_quickdraw(nns, W, torch)
+            else:
+                experiment_eps(nns, W, torch, n,
+                               "bf16x2" if args.precision == "auto" else args.precision)
+        return
     pk = peaks()
 
     host = W.lognormal_dup_f32(n, seed=2, sigma=2.0)

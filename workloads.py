@@ -21,6 +21,8 @@ Workloads (the paper's Experimental Study uses uniform, normal and lognormal 64-
   uniform / normal / lognormal / exponential.
 - ``serving_requests`` float64 request arrays of log-uniform sizes from mixed distributions with
   Poisson arrival times.
+- ``shift_mix_f32``    uniform float32 keys with a share replaced by normal "noise" (Exp-3).
+- ``uniform_u64``      uint64 keys uniform over the full range (the QuickDraw-sized stand-in, Exp-2).
 """
 from __future__ import annotations
 
@@ -206,3 +208,26 @@ def serving_requests(count: int = 1000, seed: int = 5, lo: int = 10_000, hi: int
             kind = "clustered"
         reqs.append({"arrival_s": float(arrivals[j]), "kind": kind, "keys": keys.astype(np.float64)})
     return reqs
+
+
+def shift_mix_f32(n: int, noise_frac: float, seed: int = 6, mu: float = 0.5,
+                  sigma: float = 0.1) -> np.ndarray:
+    """float32 keys for the changing-distribution experiment (Exp-3): U[0,1) draws with a share
+    `noise_frac` replaced by normal(mu, sigma) draws (the "noise"), shuffled. The paper does not
+    state the normal's parameters; N(0.5, 0.1) keeps the noise inside the uniform range, so it
+    crowds keys into the middle instead of widening the range."""
+    n_noise = int(round(n * noise_frac))
+    keys = np.empty(n, dtype=np.float32)
+    keys[:n - n_noise] = uniform_f32(n - n_noise, stream_seed(seed, 1))
+    if n_noise:
+        keys[n - n_noise:] = normal_f32(n_noise, stream_seed(seed, 2), mu, sigma)
+    return _permute_inplace(keys, seed)
+
+
+QUICKDRAW_RECORDS = 50_426_265
+
+
+def uniform_u64(n: int, seed: int = 7) -> np.ndarray:
+    """uint64 keys uniform over [0, 2^64): the stand-in for the QuickDraw key-ids (Exp-2), whose
+    records are not available here; QUICKDRAW_RECORDS is the dataset's size."""
+    return _chunked(n, lambda s, c: rng_u64(seed, s, c), np.uint64)
