@@ -5,11 +5,12 @@
 //     and the conflict arrays' arrival order intact inside a bucket), and
 //   * by the key's order image, as the radix sort behind the training sample (Sec. "Training").
 //
-// One pass reads and writes each element once. A tile ranks its elements per digit stably with
-// warp match/popc, publishes its per-digit counts, and learns its global offsets by decoupled
-// look-back over earlier tiles (tiles are numbered by an atomic ticket, so every tile waited on
-// has already started). Writes go out through a shared-memory reorder buffer in digit order, so
-// each digit's run leaves as coalesced stores.
+// One pass reads and writes each element once. A tile ranks its elements per digit stably (a warp
+// finds the lanes holding the same digit from one ballot per digit bit, then counts them with popc),
+// publishes its per-digit counts, and learns its global offsets by decoupled look-back over earlier
+// tiles, four at a time (tiles are numbered by an atomic ticket, so every tile waited on has already
+// started). Writes go out through a shared-memory reorder buffer in digit order, so each digit's
+// run leaves as coalesced stores.
 #include <algorithm>
 #include <type_traits>
 
@@ -92,7 +93,18 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
                 d = (gsv[r] >> a.shift) & mask;
         }
         dig[r] = (uint16_t)d;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        // lanes with the same digit: one ballot per digit bit (cheaper than a match on this part;
+        // in a partial tile the invalid lanes are told apart by one more ballot)
+        unsigned peers = 0xFFFFFFFFu;
+        if (cnt_tile != PART_TILE) {
+            peers = __ballot_sync(0xFFFFFFFFu, valid);
+            if (!valid) peers = ~peers;
+        }
+        for (int b = 0; b < a.bits; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, bit);
+            peers &= bit ? bal : ~bal;
+        }
         uint32_t c = 0;
         if (valid) c = S.cnt[w][d];
         __syncwarp();
@@ -123,18 +135,32 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
             st_release_u64(lb, lb_pack(a.epoch, FLAG_INCL, total));
         } else {
             st_release_u64(lb, lb_pack(a.epoch, FLAG_AGG, total));
+            // four predecessors per round trip: their words are read together (each word carries
+            // its own flag and value, so no ordering between them is needed), then taken in order
+            // until an inclusive prefix ends the walk or a tile that has not published stops it
+            constexpr int LBW = 4;
             long long p = (long long)tile - 1;
             unsigned long long t0 = 0;
-            while (p >= 0) {
-                const unsigned long long v =
-                    ld_acquire_u64(a.lookback + (size_t)p * RADIX_BINS + tid);
-                const unsigned long long flag = (v >> 46) & 3ull;
-                if ((uint32_t)(v >> 48) == (a.epoch & 0xFFFFu) && flag != 0) {
-                    excl += v & VAL_MASK;
-                    if (flag == FLAG_INCL) break;
-                    --p;
-                    continue;
+            bool done = false;
+            while (!done) {
+                unsigned long long v[LBW];
+#pragma unroll
+                for (int q = 0; q < LBW; ++q)
+                    v[q] = (p - q >= 0) ? ld_relaxed_u64(a.lookback + (size_t)(p - q) * RADIX_BINS + tid)
+                                        : 0ull;
+                int used = 0;
+#pragma unroll
+                for (int q = 0; q < LBW; ++q) {
+                    if (used != q || p - q < 0) break;
+                    const unsigned long long flag = (v[q] >> 46) & 3ull;
+                    if ((uint32_t)(v[q] >> 48) != (a.epoch & 0xFFFFu) || flag == 0) break;
+                    excl += v[q] & VAL_MASK;
+                    used = q + 1;
+                    if (flag == FLAG_INCL) { done = true; break; }
                 }
+                p -= used;
+                if (done || p < 0) break;  // tile 0 publishes an inclusive prefix: p < 0 is not reached
+                if (used) continue;
                 const unsigned long long now = globaltimer_ns();
                 if (t0 == 0) t0 = now;
                 else if (now - t0 > SPIN_LIMIT_NS) {
