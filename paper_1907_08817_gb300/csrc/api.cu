@@ -449,7 +449,7 @@ struct SegIn {
 struct Layout {
     Seg *segs; SegStats *stats; uint32_t *err; uint32_t *hist; uint32_t *bases; uint32_t *tickets;
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2]; uint32_t *row[2]; uint32_t *out_rows;
-    uint8_t *rank; uint8_t *g_flag; uint32_t *g_x, *g_y, *g_r; uint32_t *bstart;
+    uint8_t *rank; uint8_t *g_flag; uint32_t *g_x, *g_y; uint32_t *bstart;
     OKey *bmax, *carry, *blo, *bhi;
     SeamRange *ranges; uint32_t *seam_cnt;
     uint32_t *order, *order_cnt;
@@ -479,7 +479,6 @@ Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, boo
     L.g_flag = c.take<uint8_t>(N);
     L.g_x = c.take<uint32_t>(N);
     L.g_y = c.take<uint32_t>(N);
-    L.g_r = c.take<uint32_t>(N);
     L.bstart = c.take<uint32_t>((size_t)NB + 1);
     L.bmax = c.take<OKey>((size_t)NB * MAXR);
     L.carry = c.take<OKey>((size_t)NB * MAXR);
@@ -888,7 +887,6 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     sa.g_flag = L.g_flag;
     sa.g_x = L.g_x;
     sa.g_y = L.g_y;
-    sa.g_r = L.g_r;
     sa.fate = o.d_fate;
     sa.out_rows = L.out_rows;
     sa.key_scratch = L.key[oi];

@@ -472,6 +472,92 @@ __device__ Idx *cta_radix_sort(Idx *src, Idx *dst, uint32_t cnt, int keybits, Ke
     return src;
 }
 
+// Stable sort of an index list by a 32- or 64-bit key in one counting pass, for lists whose keys
+// spread evenly over their range (a bucket's elements under a fitted model). The range
+// [kmin, kmax] is cut into NBIN bins of 2^s consecutive key values; every element drops into its
+// bin (shared-memory atomics, so in arbitrary order inside it), and each element's place inside its
+// bin is then the number of the bin's elements before it in (key, index) order -- counts that are
+// independent of one another, so all threads rank their elements at once. `src` must list indices
+// in increasing order, so that index order is list order and the result is stable. Returns the
+// buffer holding the result (src), or nullptr, having changed neither list, when some bin would
+// hold more than BIN_MAX elements (the caller then sorts by radix).
+constexpr uint32_t NBIN = 4096;
+constexpr uint32_t BIN_MAX = 24;
+constexpr uint32_t BIN_SORT_MAX = 6144;  // longest list sorted this way (1.5 elements per bin)
+template <typename Idx, typename KeyFn>
+__device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_t *bins /*[NBIN]*/,
+                             unsigned long long *mm /*[2 * SNW]*/, uint32_t *scratch /*33*/) {
+    static_assert(NBIN % SOLVE_THREADS == 0, "whole bins per thread");
+    constexpr int BPT = NBIN / SOLVE_THREADS;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
+        const unsigned long long k = kf(src[i]);
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+        lo = l2 < lo ? l2 : lo;
+        hi = h2 > hi ? h2 : hi;
+    }
+    if (lane == 0) { mm[w] = lo; mm[SNW + w] = hi; }
+    for (uint32_t b = tid; b < NBIN; b += SOLVE_THREADS) bins[b] = 0;
+    __syncthreads();
+    lo = mm[0];
+    hi = mm[SNW];
+#pragma unroll
+    for (int q = 1; q < SNW; ++q) {
+        lo = mm[q] < lo ? mm[q] : lo;
+        hi = mm[SNW + q] > hi ? mm[SNW + q] : hi;
+    }
+    const unsigned long long range = hi - lo;
+    const int sh = range < NBIN ? 0 : (64 - __clzll((long long)range)) - 12;  // (range >> sh) < NBIN
+    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS)
+        atomicAdd(&bins[(uint32_t)((kf(src[i]) - lo) >> sh)], 1u);
+    __syncthreads();
+    uint32_t tsum = 0, tmax = 0;
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {
+        const uint32_t c = bins[tid * BPT + q];
+        tsum += c;
+        tmax = c > tmax ? c : tmax;
+    }
+    if (__syncthreads_or(tmax > BIN_MAX)) return nullptr;
+    uint32_t run = block_excl_sum(tsum, scratch, nullptr);
+#pragma unroll
+    for (int q = 0; q < BPT; ++q) {  // bins[b] = first slot of bin b
+        const uint32_t c = bins[tid * BPT + q];
+        bins[tid * BPT + q] = run;
+        run += c;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
+        const Idx x = src[i];
+        dst[atomicAdd(&bins[(uint32_t)((kf(x) - lo) >> sh)], 1u)] = x;
+    }
+    __syncthreads();
+    // bins[b] is now one past the last slot of bin b; each element's rank inside its bin gives its
+    // slot, written back to src (whose identity list is no longer needed)
+    for (uint32_t j = tid; j < cnt; j += SOLVE_THREADS) {
+        const Idx x = dst[j];
+        const unsigned long long kx = kf(x);
+        const uint32_t b = (uint32_t)((kx - lo) >> sh);
+        const uint32_t st = b ? bins[b - 1] : 0u, e = bins[b];
+        uint32_t r = 0;
+        for (uint32_t i = st; i < e; ++i) {
+            const Idx y = dst[i];
+            const unsigned long long ky = kf(y);
+            r += (ky < kx || (ky == kx && y < x)) ? 1u : 0u;
+        }
+        src[st + r] = x;
+    }
+    __syncthreads();
+    return src;
+}
+
 // merge two lists sorted under `less` (a strict total order) into C; caller synchronises
 template <typename Idx, typename Less>
 __device__ void cta_merge(const Idx *A, uint32_t na, const Idx *B, uint32_t nb, Idx *C, Less less) {
@@ -494,11 +580,16 @@ __device__ void cta_merge(const Idx *A, uint32_t na, const Idx *B, uint32_t nb, 
 // ---------------------------------------------------------------------------------------------
 // k_polish
 struct PolishSmem {
-    uint32_t hist[8 * 256];
-    uint32_t wcnt[SNW * 256];
+    union {
+        struct {
+            uint32_t hist[8 * 256];
+            uint32_t wcnt[SNW * 256];
+        };
+        uint32_t bins[NBIN];  // cta_bin_sort
+    };
+    unsigned long long mm[2 * SNW];
     uint32_t scratch[33];
     KMax kscratch[33];
-    uint32_t rl_off[MAXR + 1];
     KMax carry[MAXR];
     unsigned int ooo[MAXR];
     int seg, t;
@@ -514,7 +605,7 @@ struct BucketView {
     uint8_t *F;           // 1: sorted as leftover (last conflict array or out of order)
     const uint32_t *P;    // payload (nullable)
     const uint32_t *T;    // rows (nullable)
-    Idx *X, *Y, *RL, *TB;
+    Idx *X, *Y, *TB;
     uint32_t wm;
     int dtype;
     __device__ __forceinline__ uint32_t ls(uint32_t i) const { return S16 ? S16[i] : (G[i] & wm); }
@@ -526,10 +617,10 @@ struct BucketView {
     }
 };
 
-// Fig. "Algorithm polish", first part: for each o_r its stored elements in position order, the
-// out-of-order split against the running maximum (carry from earlier buckets first) and the
-// in-order run R_r (appended to v.RL, offsets in sm.rl_off). Sets v.F for leftover elements (last
-// conflict array and out-of-order ones) and counts the out-of-order ones in sm.ooo.
+// Fig. "Algorithm polish", first part: for each o_r its stored elements in position order and the
+// out-of-order split against the running maximum (carry from earlier buckets first); the in-order
+// rest is the run R_r. Sets v.F for leftover elements (last conflict array and out-of-order ones)
+// and counts the out-of-order ones in sm.ooo.
 template <typename W, typename Idx>
 __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx> &v,
                             uint32_t b, uint32_t nbk) {
@@ -551,7 +642,6 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
             if (i < nbk) v.F[i] = (rv[q] >= t) ? 1 : 0;
         }
     }
-    if (tid <= MAXR) sm.rl_off[tid] = 0;
     if (tid < MAXR) sm.ooo[tid] = 0;
     if (tid < t) {
         const OKey cr = a.carry[(size_t)b * MAXR + tid];
@@ -560,7 +650,6 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
         sm.carry[tid].valid = cr.valid;
     }
     __syncthreads();
-    uint32_t rl_n = 0;
     for (int r = 0; r < t; ++r) {
         // o_r: stored elements in position order
         for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) v.TB[j] = EMPTY;
@@ -599,7 +688,7 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
         {
             run = kmax(sm.carry[r], run);
         }
-        uint32_t kept = 0, evicted = 0;
+        uint32_t evicted = 0;
         for (uint32_t q = q0; q < q1; ++q) {
             const uint32_t x = v.Y[q];
             const unsigned long long xk = v.ok(x);
@@ -609,18 +698,9 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
                 ++evicted;
             } else {
                 run.k = xk; run.tb = xt; run.valid = 1;
-                ++kept;
             }
         }
         if (evicted) atomicAdd(&sm.ooo[r], evicted);
-        uint32_t nkept;
-        uint32_t ko = block_excl_sum(kept, sm.scratch, &nkept);
-        for (uint32_t q = q0; q < q1; ++q) {
-            const uint32_t x = v.Y[q];
-            if (!v.F[x]) v.RL[rl_n + ko++] = (Idx)x;
-        }
-        rl_n += nkept;
-        if (tid == 0) sm.rl_off[r + 1] = rl_n;
         __syncthreads();
     }
 }
@@ -632,31 +712,17 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
     const int t = sm.t;
     const int keybits = (a.key_bytes == 4) ? 32 : 64;
     polish_runs<W, Idx>(a, sm, v, b, nbk);
-    // leftover: the last conflict array and every out-of-order element, in input order
-    const uint32_t per_e = (nbk + SOLVE_THREADS - 1) / SOLVE_THREADS;
-    const uint32_t e0 = std::min(nbk, tid * per_e), e1 = std::min(nbk, e0 + per_e);
-    uint32_t lc = 0;
-    for (uint32_t i = e0; i < e1; ++i) lc += v.F[i];
-    uint32_t nl;
-    uint32_t lo_ = block_excl_sum(lc, sm.scratch, &nl);
-    for (uint32_t i = e0; i < e1; ++i)
-        if (v.F[i]) v.X[lo_++] = (Idx)i;
+    // The bucket's output -- the leftover (the last conflict array and every out-of-order element)
+    // sorted by QuickSort(w) and merged with the in-order runs R_1..R_t of Fig. "Algorithm polish" --
+    // is all of its elements in (key, row) order, so it is computed as one stable sort of the whole
+    // bucket; the runs above supply the out-of-order counts and the fates.
+    for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.X[i] = (Idx)i;
     __syncthreads();
-    // QuickSort(w): stable radix sort by key (input order breaks ties, i.e. (key, row) order)
     auto kf = [&](Idx x) -> unsigned long long { return v.ok(x); };
-    Idx *A = cta_radix_sort<Idx>(v.X, v.Y, nl, keybits, kf, sm.hist, sm.wcnt, sm.scratch);
-    Idx *Bf = (A == v.X) ? v.Y : v.X;
+    Idx *A = nbk <= BIN_SORT_MAX ? cta_bin_sort<Idx>(v.X, v.Y, nbk, kf, sm.bins, sm.mm, sm.scratch)
+                                 : nullptr;
+    if (!A) A = cta_radix_sort<Idx>(v.X, v.Y, nbk, keybits, kf, sm.hist, sm.wcnt, sm.scratch);
     __syncthreads();
-    // polish: A' <- merge(A', R_i), i = 1..t
-    uint32_t na = nl;
-    auto lessf = [&](Idx x, Idx y) { return v.less(x, y); };
-    for (int r = 0; r < t; ++r) {
-        const uint32_t r0 = sm.rl_off[r], r1 = sm.rl_off[r + 1];
-        cta_merge<Idx>(A, na, v.RL + r0, r1 - r0, Bf, lessf);
-        __syncthreads();
-        na += r1 - r0;
-        Idx *tmp = A; A = Bf; Bf = tmp;
-    }
     // write the bucket's sorted run in place of the caller's array
     const uint64_t off = (uint64_t)s0 - sg.ebase;
     W *outk = reinterpret_cast<W *>(sg.keys) + off;
@@ -687,7 +753,7 @@ int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks
                     size_t *smem_bytes) {
     const size_t fixed = sizeof(PolishSmem) + 256;
     const size_t tbl = ((size_t)2 << wlog);  // on chip the position table holds 16-bit indices
-    const size_t per = key_bytes + 2 + 1 + 1 + (payload ? 4 : 0) + (rows ? 4 : 0) + 3 * 2;
+    const size_t per = key_bytes + 2 + 1 + 1 + (payload ? 4 : 0) + (rows ? 4 : 0) + 2 * 2;
     // shared memory per SM is 228 KB (227 KB usable by one block); each resident block reserves
     // 1 KB. When the position table leaves no room at this many blocks per SM, fewer blocks share
     // the SM; with no room even for one block every bucket takes the global-memory path.
@@ -730,7 +796,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
         uint32_t *TB = reinterpret_cast<uint32_t *>(dyn);
         BucketView<W, uint32_t> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
                                   a.rank + s0, a.g_flag + s0, nullptr, nullptr, a.g_x + s0, a.g_y + s0,
-                                  a.g_r + s0, TB, Wn - 1u, a.dtype};
+                                  TB, Wn - 1u, a.dtype};
         polish_runs<W, uint32_t>(a, sm, v, b, nbk);
         if (tid < sm.t && sm.ooo[tid]) atomicAdd(&a.stats[sm.seg].ooo[tid], (unsigned long long)sm.ooo[tid]);
         if (tid == 0) {
@@ -751,7 +817,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
         uint16_t *S16 = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
         uint16_t *X = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
         uint16_t *Y = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
-        uint16_t *RL = reinterpret_cast<uint16_t *>(p); p += (size_t)2 * cap;
         uint8_t *R = p; p += cap;
         uint8_t *F = p; p += cap;
         const W *gk = reinterpret_cast<const W *>(a.keys) + s0;
@@ -786,7 +851,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
             }
         }
         __syncthreads();
-        BucketView<W, uint16_t> v{K, S16, nullptr, R, F, P, T, X, Y, RL, TB, Wn - 1u, a.dtype};
+        BucketView<W, uint16_t> v{K, S16, nullptr, R, F, P, T, X, Y, TB, Wn - 1u, a.dtype};
         polish_bucket<W, uint16_t>(a, sm, v, b, s0, nbk, sg);
     } else {
         if (tid == 0) atomicAdd(&a.stats[sm.seg].oversized, 1u);
@@ -794,7 +859,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
         BucketView<W, uint32_t> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
                                   a.rank + s0, a.g_flag + s0, a.pay ? a.pay + s0 : nullptr,
                                   a.rows ? a.rows + s0 : nullptr, a.g_x + s0, a.g_y + s0,
-                                  a.g_r + s0, TB, Wn - 1u, a.dtype};
+                                  TB, Wn - 1u, a.dtype};
         polish_bucket<W, uint32_t>(a, sm, v, b, s0, nbk, sg);
     }
 }

@@ -35,8 +35,8 @@ namespace {
 constexpr uint64_t NA_MAX_N = NNSORT_NOALLOC_MAX_N;
 constexpr uint32_t NA_MAX_BUCKETS = 1024;
 constexpr uint64_t NA_MAX_TILES = (NA_MAX_N + PART_TILE - 1) / PART_TILE;
-constexpr size_t NA_PER_ELEM = 2 * 4 + 2 * 8 + 2 * 4 + 1 + 1 + 3 * 4;  // gs, keys, payload, rank,
-                                                                      // flag, three index lists
+constexpr size_t NA_PER_ELEM = 2 * 4 + 2 * 8 + 2 * 4 + 1 + 1 + 2 * 4;  // gs, keys, payload, rank,
+                                                                      // flag, two index lists
 constexpr size_t NA_BYTES = NA_MAX_N * NA_PER_ELEM + (size_t)NA_MAX_BUCKETS * (4 + 2 * MAXR * 16 + 32) +
                             NA_MAX_TILES * RADIX_BINS * 8 + 2 * MAX_PASSES * RADIX_BINS * 4 +
                             (size_t)(NA_MAX_BUCKETS + 1) * sizeof(SeamRange) + 64 * 1024;
@@ -66,7 +66,7 @@ size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 struct NaLayout {
     Seg *seg; SegStats *stats; uint32_t *err, *hist, *bases, *tickets;
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2];
-    uint8_t *rank, *flag; uint32_t *gx, *gy, *gr, *bstart;
+    uint8_t *rank, *flag; uint32_t *gx, *gy, *bstart;
     OKey *bmax, *carry, *blo, *bhi;
     SeamRange *ranges; uint32_t *seam_cnt;
     unsigned long long *lookback;
@@ -92,7 +92,6 @@ NaLayout na_carve(unsigned char *b) {
     L.flag = take(NA_MAX_N);
     L.gx = reinterpret_cast<uint32_t *>(take(4 * NA_MAX_N));
     L.gy = reinterpret_cast<uint32_t *>(take(4 * NA_MAX_N));
-    L.gr = reinterpret_cast<uint32_t *>(take(4 * NA_MAX_N));
     L.bstart = reinterpret_cast<uint32_t *>(take(4 * (NA_MAX_BUCKETS + 1)));
     L.bmax = reinterpret_cast<OKey *>(take(sizeof(OKey) * NA_MAX_BUCKETS * MAXR));
     L.carry = reinterpret_cast<OKey *>(take(sizeof(OKey) * NA_MAX_BUCKETS * MAXR));
@@ -258,7 +257,6 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     sa.g_flag = L.flag;
     sa.g_x = L.gx;
     sa.g_y = L.gy;
-    sa.g_r = L.gr;
     sa.key_scratch = L.key[oi];
     sa.pay_scratch = pay ? L.pay[oi] : nullptr;
     sa.err = L.err;
