@@ -98,6 +98,33 @@ __device__ __forceinline__ uint32_t cvt_bf16x2_rz_relu(float first, float second
     return d;
 }
 
+// Two binary32 lanes per instruction (packed FP32 on sm_100 and later): each lane is rounded exactly
+// as the scalar operation would be; the pair (lo, hi) travels as one 64-bit register.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2_rn(unsigned long long a, unsigned long long b,
+                                                      unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long add2_rn(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sub2_rn(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -291,11 +318,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
 #pragma unroll
                 for (int g = 0; g < KPT; ++g) {
                     uint32_t hi[4], lo[4];
+                    const unsigned long long xx = pk2(x[g], x[g]);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        // pre-activations; the conversions apply the ReLU (negative results become 0)
-                        const float h0 = __fmaf_rn(w8[2 * q], x[g], b8[2 * q]);
-                        const float h1 = __fmaf_rn(w8[2 * q + 1], x[g], b8[2 * q + 1]);
+                        // pre-activations of units 2q, 2q+1 in one packed FMA; the conversions apply
+                        // the ReLU (negative results become 0)
+                        const unsigned long long hh =
+                            fma2_rn(pk2(w8[2 * q], w8[2 * q + 1]), xx, pk2(b8[2 * q], b8[2 * q + 1]));
+                        float h0, h1;
+                        upk2(hh, h0, h1);
                         if (!SPLIT) {
                             hi[q] = cvt_bf16x2_rn_relu(h0, h1);  // RN(ReLU(h))
                         } else {
@@ -303,8 +334,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                             // lo = the rest (non-negative, exact in binary32) rounded to FP16 (11
                             // bits); for h <= 0 both parts are 0
                             hi[q] = cvt_bf16x2_rz_relu(h0, h1);
-                            const float r0 = __fsub_rn(h0, __uint_as_float(__float_as_uint(h0) & 0xFFFF0000u));
-                            const float r1 = __fsub_rn(h1, __uint_as_float(__float_as_uint(h1) & 0xFFFF0000u));
+                            const unsigned long long tr =
+                                pk2(__uint_as_float(__float_as_uint(h0) & 0xFFFF0000u),
+                                    __uint_as_float(__float_as_uint(h1) & 0xFFFF0000u));
+                            float r0, r1;
+                            upk2(sub2_rn(hh, tr), r0, r1);
                             lo[q] = cvt_f16x2_rn_relu(r0, r1);
                         }
                     }
@@ -343,9 +377,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
             phase ^= 1u;
             dead = __syncthreads_or(dead);
             tc_fence_after();
-            float yy[KPT];
+            // output layer in two packed partial sums (even and odd hidden units), added at the end
+            unsigned long long yy[KPT];
 #pragma unroll
-            for (int g = 0; g < KPT; ++g) yy[g] = pf[4 * H];
+            for (int g = 0; g < KPT; ++g) yy[g] = pk2(pf[4 * H], 0.0f);
 #pragma unroll
             for (int c0 = 0; c0 < H; c0 += 16) {
                 float b2[16], w3[16];
@@ -366,14 +401,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                         for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
                     }
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        yy[g] = __fmaf_rn(w3[q], relu_f(__fadd_rn(acc[q], b2[q])), yy[g]);
+                    for (int q = 0; q < 16; q += 2) {
+                        float t0, t1;
+                        upk2(add2_rn(pk2(acc[q], acc[q + 1]), pk2(b2[q], b2[q + 1])), t0, t1);
+                        yy[g] = fma2_rn(pk2(w3[q], w3[q + 1]), pk2(relu_f(t0), relu_f(t1)), yy[g]);
+                    }
                 }
             }
 #pragma unroll
             for (int g = 0; g < KPT; ++g) {
-                y[g] = yy[g];
-                slot[g] = slot_of(yy[g], sg.nm_hi, sg.nm_lo, sg.L);
+                float ye, yo;
+                upk2(yy[g], ye, yo);
+                y[g] = __fadd_rn(ye, yo);
+                slot[g] = slot_of(y[g], sg.nm_hi, sg.nm_lo, sg.L);
             }
             tc_fence_before();
         } else {
