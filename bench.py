@@ -41,10 +41,10 @@ WORKLOAD = ("268,435,456 float32 keys lognormal(0,2) with 5% exact duplicates, k
 # DRAM bytes per key of one launch, from the ncu captures summarised under profiles/ (2^26 keys,
 # same distribution and model recipe; traffic grows in proportion to the keys)
 TRAFFIC_PER_KEY = {
-    ("predict", "bf16x2"): 7.374,   # profiles/k_predict_bf16_split_64M.md
+    ("predict", "bf16x2"): 7.380,   # profiles/k_predict_bf16_split_64M.md
     ("rounds", None): 6.805,        # profiles/k_rounds_64M.md
-    ("polish", None): 12.647,       # profiles/k_polish_64M.md
-    ("partition", None): 15.560,    # profiles/k_onesweep_partition_64M.md (per pass)
+    ("polish", None): 12.657,       # profiles/k_polish_64M.md
+    ("partition", None): 15.566,    # profiles/k_onesweep_partition_64M.md (per pass)
 }
 # binary32 operations per key on the CUDA cores in the tensor-core predict (layer 1: H FMA; split
 # form: H residual subtractions; output layer: H additions and H FMA; FMA = 2)
