@@ -300,11 +300,14 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
     // dW2 tile: rows k0..k0+TK-1, columns j0..j0+TN-1 over the H x H gradient
     constexpr int TK = (H * H) / (TR_THREADS * TN);  // 4 for H = 64, 2 for H = 32
     const int k0 = TK * tm, j0 = TN * tn;
-    float aW2[TK][TN];
+    // accumulators hold column pairs (q, q+1) for the packed two-lane FMA: each lane is rounded as a
+    // scalar FMA would be, so the sums are those of the scalar loop
+    constexpr int TP = TN / 2;
+    unsigned long long aW2[TK][TP];
 #pragma unroll
     for (int i = 0; i < TK; ++i)
 #pragma unroll
-        for (int q = 0; q < TN; ++q) aW2[i][q] = 0.0f;
+        for (int q = 0; q < TP; ++q) aW2[i][q] = 0ull;
     float aV = 0.0f, aV2 = 0.0f;  // per-thread vector gradients (see the role split below)
     float lacc = 0.0f;
     const uint64_t per = (g.n + gridDim.x - 1) / gridDim.x;
@@ -330,27 +333,33 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
         }
         __syncthreads();
         {   // Z = b2 + H1 W2^T, then H2 = relu(Z)
-            float acc[4][TN];
+            unsigned long long acc[4][TP];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int q = 0; q < TN; ++q) acc[i][q] = b2[n0 + q];
+                for (int q = 0; q < TP; ++q) acc[i][q] = pk2(b2[n0 + 2 * q], b2[n0 + 2 * q + 1]);
 #pragma unroll 8
             for (int j = 0; j < H; ++j) {
-                float a[4], b[TN];
+                unsigned long long b[TP];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = sH1[(m0 + i) * LD + j];
+                for (int q = 0; q < TP; ++q) b[q] = pk2(W2T[j * LD + n0 + 2 * q], W2T[j * LD + n0 + 2 * q + 1]);
 #pragma unroll
-                for (int q = 0; q < TN; ++q) b[q] = W2T[j * LD + n0 + q];
+                for (int i = 0; i < 4; ++i) {
+                    const float av = sH1[(m0 + i) * LD + j];
+                    const unsigned long long a2 = pk2(av, av);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int q = 0; q < TN; ++q) acc[i][q] = __fmaf_rn(b[q], a[i], acc[i][q]);
+                    for (int q = 0; q < TP; ++q) acc[i][q] = fma2_rn(b[q], a2, acc[i][q]);
+                }
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int q = 0; q < TN; ++q) sH2[(m0 + i) * LD + n0 + q] = relu_f(acc[i][q]);
+                for (int q = 0; q < TP; ++q) {
+                    float z0, z1;
+                    upk2(acc[i][q], z0, z1);
+                    sH2[(m0 + i) * LD + n0 + 2 * q] = relu_f(z0);
+                    sH2[(m0 + i) * LD + n0 + 2 * q + 1] = relu_f(z1);
+                }
         }
         __syncthreads();
         if (tid < GC) {  // output, loss, upstream gradient per sample
@@ -383,28 +392,34 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
         }
         __syncthreads();
         {   // D1 = [H1 > 0] (D2 W2)
-            float acc[4][TN];
+            unsigned long long acc[4][TP];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int q = 0; q < TN; ++q) acc[i][q] = 0.0f;
+                for (int q = 0; q < TP; ++q) acc[i][q] = 0ull;
 #pragma unroll 8
             for (int k = 0; k < H; ++k) {
-                float a[4], b[TN];
+                unsigned long long b[TP];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = sD2[(m0 + i) * LD + k];
+                for (int q = 0; q < TP; ++q) b[q] = pk2(W2[k * H + n0 + 2 * q], W2[k * H + n0 + 2 * q + 1]);
 #pragma unroll
-                for (int q = 0; q < TN; ++q) b[q] = W2[k * H + n0 + q];
+                for (int i = 0; i < 4; ++i) {
+                    const float av = sD2[(m0 + i) * LD + k];
+                    const unsigned long long a2 = pk2(av, av);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int q = 0; q < TN; ++q) acc[i][q] = __fmaf_rn(a[i], b[q], acc[i][q]);
+                    for (int q = 0; q < TP; ++q) acc[i][q] = fma2_rn(a2, b[q], acc[i][q]);
+                }
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int q = 0; q < TN; ++q)
-                    sD1[(m0 + i) * LD + n0 + q] = (sH1[(m0 + i) * LD + n0 + q] > 0.0f) ? acc[i][q] : 0.0f;
+                for (int q = 0; q < TP; ++q) {
+                    float d0, d1;
+                    upk2(acc[i][q], d0, d1);
+                    const int c = (m0 + i) * LD + n0 + 2 * q;
+                    sD1[c] = (sH1[c] > 0.0f) ? d0 : 0.0f;
+                    sD1[c + 1] = (sH1[c + 1] > 0.0f) ? d1 : 0.0f;
+                }
         }
         __syncthreads();
         if (g.gx && tid < cn) {
@@ -415,15 +430,16 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
         // dW2 += D2^T H1 over this chunk's samples
 #pragma unroll 4
         for (int s = 0; s < cn; ++s) {
-            float a[TK], b[TN];
+            unsigned long long b[TP];
 #pragma unroll
-            for (int i = 0; i < TK; ++i) a[i] = sD2[s * LD + k0 + i];
+            for (int q = 0; q < TP; ++q) b[q] = pk2(sH1[s * LD + j0 + 2 * q], sH1[s * LD + j0 + 2 * q + 1]);
 #pragma unroll
-            for (int q = 0; q < TN; ++q) b[q] = sH1[s * LD + j0 + q];
+            for (int i = 0; i < TK; ++i) {
+                const float av = sD2[s * LD + k0 + i];
+                const unsigned long long a2 = pk2(av, av);
 #pragma unroll
-            for (int i = 0; i < TK; ++i)
-#pragma unroll
-                for (int q = 0; q < TN; ++q) aW2[i][q] = __fmaf_rn(a[i], b[q], aW2[i][q]);
+                for (int q = 0; q < TP; ++q) aW2[i][q] = fma2_rn(a2, b[q], aW2[i][q]);
+            }
         }
         // vectors: t < H -> (db2_t, dW3_t); H <= t < 2H -> (db1_j, dW1_j); t == 2H -> db3
         if (tid < H) {
@@ -448,7 +464,12 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
 #pragma unroll
     for (int i = 0; i < TK; ++i)
 #pragma unroll
-        for (int q = 0; q < TN; ++q) out[2 * H + (k0 + i) * H + j0 + q] = aW2[i][q];
+        for (int q = 0; q < TP; ++q) {
+            float w0, w1;
+            upk2(aW2[i][q], w0, w1);
+            out[2 * H + (k0 + i) * H + j0 + 2 * q] = w0;
+            out[2 * H + (k0 + i) * H + j0 + 2 * q + 1] = w1;
+        }
     if (tid < H) {
         out[2 * H + H * H + tid] = aV;       // b2
         out[3 * H + H * H + tid] = aV2;      // W3
