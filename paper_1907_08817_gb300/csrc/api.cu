@@ -829,6 +829,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     pa.key_bytes = kb;
     pa.dtype = dtype;
     pa.pwl = pwl_dev;
+    pa.single_model = (single && f0 && !o.d_slots) ? 1 : 0;
     const PadArch arch = f0 ? f0->pad : pad_arch(1, 8, 0);
     const int prec = f0 ? o.precision : NNSORT_PREC_FP32;
     {
@@ -1161,6 +1162,7 @@ int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_m
     pa.key_bytes = key_bytes_of(dtype);
     pa.dtype = dtype;
     pa.pwl = pwl_dev;
+    pa.single_model = 1;
     w->last_err = err;
     cudaError_t e = launch_predict(f->pad, precision, pa, sm_count(), stream);
     if (e == cudaErrorNotSupported) return NNSORT_E_UNSUPPORTED;

@@ -71,6 +71,7 @@ struct PredictArgs {
     int key_bytes;
     int dtype;
     PwlDev pwl;              // NNSORT_PREC_PWL (single array)
+    int single_model;        // 1: one array whose positions come from its model (no injected slots)
 };
 cudaError_t launch_predict(const PadArch &a, int precision, const PredictArgs &p, int sms,
                            cudaStream_t s);

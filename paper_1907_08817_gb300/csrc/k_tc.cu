@@ -430,6 +430,242 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
         if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
 }
 
+// ---------------------------------------------------------------------------------------------
+// One array, one model: NG independent groups of 4 warps per block and one block per SM. Group g
+// has its own A tile(s), accumulator columns [g H, (g + 1) H), mbarrier and named barrier (1 + g)
+// and walks its own sub-tiles of 128 keys; the B tile(s) and the parameters are staged once per
+// block and shared. The A tiles are then the only per-group shared memory, so NG = 6 groups fit
+// on an SM (24 warps, against 16 for blocks that each hold a W2 copy), and no block-wide barrier
+// separates one sub-tile from the next.
+constexpr int TC_NG = 6;
+
+__device__ __forceinline__ void grp_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(TC_THREADS) : "memory");
+}
+// OR of v over the 128 threads of named barrier id (a barrier as well)
+__device__ __forceinline__ bool grp_or(int id, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "n"(TC_THREADS)
+        : "memory");
+    return r != 0;
+}
+
+template <int H, bool SPLIT, int NG>
+__host__ __device__ constexpr size_t tcmg_smem_bytes(int npass) {
+    return (size_t)NG * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)(SPLIT ? 2 : 1) * H * H * 2 +
+           (size_t)(4 * H + 4) * 4 + (size_t)npass * RADIX_BINS * 4;
+}
+
+template <int H, typename W, bool SPLIT, int NG>
+__global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictArgs a) {
+    static_assert(H == 16 || H == 32 || H == 64, "tensor path widths");
+    static_assert(NG * H <= 512, "accumulators fit in tensor memory");
+    constexpr int NT = SPLIT ? 2 : 1;
+    constexpr uint32_t TILE_B = TC_M * H * 2;
+    constexpr uint32_t LBO = 128;
+    constexpr uint32_t SBO = (H / 8) * 128;
+    constexpr int NCOL = NG * H <= 128 ? 128 : (NG * H <= 256 ? 256 : 512);
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *sB = sm + NG * NT * TILE_B;
+    unsigned char *sB16 = sB + H * H * 2;
+    float *pf = reinterpret_cast<float *>(sB + NT * H * H * 2);  // W1 | b1 | b2 | W3 | b3
+    const float4 *pv = reinterpret_cast<const float4 *>(pf);
+    uint32_t *sh_hist = reinterpret_cast<uint32_t *>(pf + 4 * H + 4);
+    __shared__ __align__(8) unsigned long long bar[NG];
+    __shared__ uint32_t tmem_base;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int grp = tid / TC_THREADS, gt = tid % TC_THREADS;
+    const int npass = a.hist ? a.plan.npass : 0;
+    for (int i = tid; i < npass * RADIX_BINS; i += NG * TC_THREADS) sh_hist[i] = 0;
+    if (warp == 0) tmem_alloc<NCOL>(smem_u32(&tmem_base));
+    if (tid == 0) {
+        for (int g = 0; g < NG; ++g) mbar_init(smem_u32(&bar[g]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const Seg &sg = a.segs[0];
+    {   // W2 (row = output unit, K = input unit) -> canonical K-major layout; parameters
+        const float *W2 = sg.params + 2 * H;
+        for (int e = tid; e < H * H; e += NG * TC_THREADS) {
+            const int nrow = e / H, k = e % H;
+            const uint32_t off = (nrow / 8) * SBO + (k / 8) * LBO + (nrow % 8) * 16 + (k % 8) * 2;
+            *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16_rn(W2[e]);
+            if (SPLIT) *reinterpret_cast<__half *>(sB16 + off) = __float2half_rn(W2[e]);
+        }
+        for (int e = tid; e < H; e += NG * TC_THREADS) {
+            pf[e] = sg.params[e];
+            pf[H + e] = sg.params[H + e];
+            pf[2 * H + e] = sg.params[2 * H + H * H + e];
+            pf[3 * H + e] = sg.params[3 * H + H * H + e];
+        }
+        if (tid == 0) pf[4 * H] = sg.params[4 * H + H * H];
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base;
+    const uint32_t dcol = tbase + (uint32_t)(grp * H);
+    const uint32_t lane_addr = dcol + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t aoff = (gt / 8) * SBO + (gt % 8) * 16;
+    unsigned char *myA = sm + grp * NT * TILE_B;
+    const uint32_t mybar = smem_u32(&bar[grp]);
+    const int bid = 1 + grp;
+    const uint32_t idesc = idesc_bf16(TC_M, H);
+    const uint32_t idesc_lo = idesc_f16(TC_M, H);
+    uint32_t phase = 0, err = 0, dead_parity = 0;
+    bool dead = false;
+    const uint64_t n = sg.n;
+    const uint64_t total = (n + TC_M - 1) / TC_M;
+    const uint64_t stride = (uint64_t)gridDim.x * NG;
+    const W *keys = reinterpret_cast<const W *>(sg.keys);
+    uint64_t pre = 0, pre_st = ~0ull;
+    for (uint64_t st = (uint64_t)blockIdx.x * NG + grp; st < total; st += stride) {
+        const uint64_t i = st * TC_M + gt;
+        const bool valid = i < n;
+        const uint64_t wv = !valid ? 0ull : (pre_st == st ? pre : word64(keys[i]));
+        if (valid && key_is_nan(wv, a.dtype)) err |= ERR_NAN;
+        {   // the group's next sub-tile's keys, loaded while this one is computed
+            const uint64_t st2 = st + stride;
+            if (st2 < total) {
+                const uint64_t i2 = st2 * TC_M + gt;
+                pre = i2 < n ? word64(keys[i2]) : 0ull;
+                pre_st = st2;
+            }
+        }
+        const float x = valid ? translate_x(wv, sg.norm) : 0.0f;
+        const unsigned long long xx = pk2(x, x);
+#pragma unroll
+        for (int j0 = 0; j0 < H; j0 += 8) {
+            const float4 wa = pv[j0 / 4], wb = pv[j0 / 4 + 1];
+            const float4 ba = pv[H / 4 + j0 / 4], bb = pv[H / 4 + j0 / 4 + 1];
+            const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned long long hh =
+                    fma2_rn(pk2(w8[2 * q], w8[2 * q + 1]), xx, pk2(b8[2 * q], b8[2 * q + 1]));
+                float h0, h1;
+                upk2(hh, h0, h1);
+                if (!SPLIT) {
+                    hi[q] = cvt_bf16x2_rn_relu(h0, h1);
+                } else {
+                    hi[q] = cvt_bf16x2_rz_relu(h0, h1);
+                    const unsigned long long tr = pk2(__uint_as_float(__float_as_uint(h0) & 0xFFFF0000u),
+                                                      __uint_as_float(__float_as_uint(h1) & 0xFFFF0000u));
+                    float r0, r1;
+                    upk2(sub2_rn(hh, tr), r0, r1);
+                    lo[q] = cvt_f16x2_rn_relu(r0, r1);
+                }
+            }
+            unsigned char *t0 = myA + aoff + (j0 / 8) * LBO;
+            *reinterpret_cast<uint4 *>(t0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            if (SPLIT) *reinterpret_cast<uint4 *>(t0 + TILE_B) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        grp_sync(bid);
+        tc_fence_after();
+        if (gt == 0 && !dead) {
+            const uint32_t a0 = smem_u32(myA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int ks = 0; ks < H / 16; ++ks)
+                mma_bf16(dcol, mdesc(a0 + ks * 2 * LBO, LBO, SBO), mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc,
+                         ks > 0 ? 1u : 0u);
+            if (SPLIT) {
+#pragma unroll
+                for (int ks = 0; ks < H / 16; ++ks)
+                    mma_bf16(dcol, mdesc(a0 + TILE_B + ks * 2 * LBO, LBO, SBO),
+                             mdesc(smem_u32(sB16) + ks * 2 * LBO, LBO, SBO), idesc_lo, 1u);
+            }
+            mma_commit(mybar);
+        }
+        if (!dead && !mbar_wait(mybar, phase)) {
+            dead = true;
+            dead_parity = phase;
+            err |= ERR_TIMEOUT;
+        }
+        phase ^= 1u;
+        dead = grp_or(bid, dead);
+        tc_fence_after();
+        unsigned long long yy = pk2(pf[4 * H], 0.0f);
+#pragma unroll
+        for (int c0 = 0; c0 < H; c0 += 16) {
+            float acc[16];
+            if (!dead) {
+                tmem_ld16(lane_addr + c0, acc);
+                tmem_wait_ld();
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float4 bq = pv[2 * H / 4 + c0 / 4 + v], wq = pv[3 * H / 4 + c0 / 4 + v];
+                float t0, t1, t2, t3;
+                upk2(add2_rn(pk2(acc[4 * v], acc[4 * v + 1]), pk2(bq.x, bq.y)), t0, t1);
+                upk2(add2_rn(pk2(acc[4 * v + 2], acc[4 * v + 3]), pk2(bq.z, bq.w)), t2, t3);
+                yy = fma2_rn(pk2(wq.x, wq.y), pk2(relu_f(t0), relu_f(t1)), yy);
+                yy = fma2_rn(pk2(wq.z, wq.w), pk2(relu_f(t2), relu_f(t3)), yy);
+            }
+        }
+        tc_fence_before();
+        if (!valid) continue;
+        float ye, yo;
+        upk2(yy, ye, yo);
+        const float y = __fadd_rn(ye, yo);
+        const uint32_t slot = slot_of(y, sg.nm_hi, sg.nm_lo, sg.L);
+        const uint64_t e = sg.ebase + i;
+        const uint32_t gpos = (uint32_t)(sg.gs_base + slot);
+        if (a.gs) a.gs[e] = gpos;
+        if (a.key_copy) reinterpret_cast<W *>(a.key_copy)[e] = (W)wv;
+        if (a.pay_copy && sg.payload) a.pay_copy[e] = (uint32_t)sg.payload[i];
+        if (a.row_init) a.row_init[e] = (uint32_t)i;
+        if (a.slots_out) a.slots_out[e] = slot;
+        if (a.y_out) a.y_out[e] = y;
+#pragma unroll
+        for (int p = 0; p < MAX_PASSES; ++p) {
+            if (p >= npass) break;
+            const uint32_t d = (gpos >> a.plan.shift[p]) & ((1u << a.plan.bits[p]) - 1u);
+            atomicAdd(&sh_hist[p * RADIX_BINS + d], 1u);
+        }
+    }
+    if (err) atomicOr(a.err, err);
+    // an MMA whose completion was not seen may still be running: wait for it (bounded) before the
+    // tensor memory it writes is released
+    if (dead && gt == 0) mbar_wait(mybar, dead_parity);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_free<NCOL>(tbase);
+    for (int i = tid; i < npass * RADIX_BINS; i += NG * TC_THREADS)
+        if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
+}
+
+template <int H, bool SPLIT>
+static cudaError_t bf16_mg_go(const PredictArgs &p, int sms, cudaStream_t s) {
+    const uint64_t n_sub = (uint64_t)p.total_tiles * (PRED_TILE / TC_M);
+    const int npass = p.hist ? p.plan.npass : 0;
+    const size_t smem = tcmg_smem_bytes<H, SPLIT, TC_NG>(npass);
+    const int grid = (int)std::min<uint64_t>((n_sub + TC_NG - 1) / TC_NG, (uint64_t)sms);
+    if (grid == 0) return cudaSuccess;
+    auto k4 = k_predict_bf16_mg<H, uint32_t, SPLIT, TC_NG>;
+    auto k8 = k_predict_bf16_mg<H, uint64_t, SPLIT, TC_NG>;
+    cudaError_t e = cudaFuncSetAttribute(p.key_bytes == 4 ? k4 : k8,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (p.key_bytes == 4) k4<<<grid, TC_NG * TC_THREADS, smem, s>>>(p);
+    else k8<<<grid, TC_NG * TC_THREADS, smem, s>>>(p);
+    return nns_launched(cudaGetLastError());
+}
+
 template <int H, bool SPLIT, int KPT>
 static cudaError_t bf16_go(const PredictArgs &p, int sms, cudaStream_t s) {
     const uint64_t subtiles = (uint64_t)p.total_tiles * (PRED_TILE / (KPT * TC_M));
@@ -463,6 +699,13 @@ constexpr int TC_KPT = 2, TC_KPT_SPLIT = 1;
 
 cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, bool split, int sms, cudaStream_t s) {
     if (a.layers != 2) return cudaErrorNotSupported;
+    if (p.nseg == 1 && p.single_model) {
+        switch (a.h1) {
+        case 16: return split ? bf16_mg_go<16, true>(p, sms, s) : bf16_mg_go<16, false>(p, sms, s);
+        case 32: return split ? bf16_mg_go<32, true>(p, sms, s) : bf16_mg_go<32, false>(p, sms, s);
+        case 64: return split ? bf16_mg_go<64, true>(p, sms, s) : bf16_mg_go<64, false>(p, sms, s);
+        }
+    }
     switch (a.h1) {
     case 16: return split ? bf16_go<16, true, TC_KPT_SPLIT>(p, sms, s) : bf16_go<16, false, TC_KPT>(p, sms, s);
     case 32: return split ? bf16_go<32, true, TC_KPT_SPLIT>(p, sms, s) : bf16_go<32, false, TC_KPT>(p, sms, s);
