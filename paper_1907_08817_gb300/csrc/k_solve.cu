@@ -889,6 +889,10 @@ __device__ __forceinline__ KMax kinv(const KMax &x) {
 // 1) k_seam_ps (one block per array): S(b) = the smallest element of the buckets after b,
 //    P(b) = the largest element of the buckets before b.
 __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_ps(SolveArgs a) {
+    // tiles of PSI * SOLVE_THREADS buckets, PSI consecutive ones per thread: a thread folds its own
+    // buckets in order and one block scan per tile carries the rest
+    constexpr int PSI = 8;
+    constexpr uint32_t PST = SOLVE_THREADS * PSI;
     __shared__ KMax ks[33];
     __shared__ KMax tot;
     const int s = blockIdx.x, tid = threadIdx.x;
@@ -896,35 +900,57 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_ps(SolveArgs a) {
     const Seg &sg = a.segs[s];
     const uint32_t nb = sg.nb, bb = sg.bbase;
     auto okey = [&](const OKey &o) { KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid; return x; };
+    KMax v[PSI];
     KMax carry = kmax_none();  // inverted minimum of the buckets after the current tile
     for (uint32_t t1 = nb; t1 > 0;) {
-        const uint32_t t0 = t1 > SOLVE_THREADS ? t1 - SOLVE_THREADS : 0;
-        const uint32_t c = t1 - 1 - tid;  // this thread's bucket (valid when tid < t1 - t0)
-        const bool own = (uint32_t)tid < t1 - t0;
-        const uint32_t bi = bb + c;
-        const bool ne = own && a.bstart[bi + 1] > a.bstart[bi];
-        const KMax v = ne ? kinv(okey(a.blo[bi])) : kmax_none();
-        const KMax ex = block_excl_max(v, ks, &tot);
-        if (ne) {
-            const KMax sv = kinv(kmax(carry, ex));
-            OKey o; o.k = sv.k; o.tb = sv.tb; o.valid = sv.valid;
-            a.seam_suf[bi] = o;
+        const uint32_t t0 = t1 > PST ? t1 - PST : 0;
+        KMax loc = kmax_none();
+        uint32_t nem = 0;  // bit k: this thread's bucket k is non-empty
+#pragma unroll
+        for (int k = 0; k < PSI; ++k) {  // this thread's buckets, later ones first
+            const uint32_t r = (uint32_t)tid * PSI + k;
+            const uint32_t bi = bb + (t1 - 1 - r);
+            const bool ne = r < t1 - t0 && a.bstart[bi + 1] > a.bstart[bi];
+            nem |= (ne ? 1u : 0u) << k;
+            v[k] = ne ? kinv(okey(a.blo[bi])) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = kmax(carry, block_excl_max(loc, ks, &tot));
+#pragma unroll
+        for (int k = 0; k < PSI; ++k) {
+            if ((nem >> k) & 1u) {
+                const uint32_t bi = bb + (t1 - 1 - ((uint32_t)tid * PSI + k));
+                const KMax sv = kinv(run);
+                OKey o; o.k = sv.k; o.tb = sv.tb; o.valid = sv.valid;
+                a.seam_suf[bi] = o;
+                run = kmax(run, v[k]);
+            }
         }
         carry = kmax(carry, tot);
         t1 = t0;
     }
     carry = kmax_none();  // maximum of the buckets before the current tile
-    for (uint32_t t0 = 0; t0 < nb; t0 += SOLVE_THREADS) {
-        const uint32_t c = t0 + tid;
-        const bool own = c < nb;
-        const uint32_t bi = bb + c;
-        const bool ne = own && a.bstart[bi + 1] > a.bstart[bi];
-        const KMax v = ne ? okey(a.bhi[bi]) : kmax_none();
-        const KMax ex = block_excl_max(v, ks, &tot);
-        if (ne) {
-            const KMax pv = kmax(carry, ex);
-            OKey o; o.k = pv.k; o.tb = pv.tb; o.valid = pv.valid;
-            a.seam_pre[bi] = o;
+    for (uint32_t t0 = 0; t0 < nb; t0 += PST) {
+        KMax loc = kmax_none();
+        uint32_t nem = 0;
+#pragma unroll
+        for (int k = 0; k < PSI; ++k) {
+            const uint32_t c = t0 + (uint32_t)tid * PSI + k;
+            const uint32_t bi = bb + c;
+            const bool ne = c < nb && a.bstart[bi + 1] > a.bstart[bi];
+            nem |= (ne ? 1u : 0u) << k;
+            v[k] = ne ? okey(a.bhi[bi]) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = kmax(carry, block_excl_max(loc, ks, &tot));
+#pragma unroll
+        for (int k = 0; k < PSI; ++k) {
+            if ((nem >> k) & 1u) {
+                const uint32_t bi = bb + t0 + (uint32_t)tid * PSI + k;
+                OKey o; o.k = run.k; o.tb = run.tb; o.valid = run.valid;
+                a.seam_pre[bi] = o;
+                run = kmax(run, v[k]);
+            }
         }
         carry = kmax(carry, tot);
     }
@@ -1001,18 +1027,35 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_emit(SolveArgs a) {
             a.ranges[atomicAdd(&a.seam_cnt[0], 1u)] = r;
         }
     };
+    // tiles of PSI * SOLVE_THREADS buckets, PSI consecutive ones per thread (later ones first)
+    constexpr int PSI = 8;
+    constexpr uint32_t PST = SOLVE_THREADS * PSI;
     KMax carry = kmax_none();  // smallest first sound cut after the current tile (inverted)
     for (uint32_t t1 = nb; t1 > 0;) {
-        const uint32_t t0 = t1 > SOLVE_THREADS ? t1 - SOLVE_THREADS : 0;
-        const uint32_t c = t1 - 1 - tid;
-        const bool own = (uint32_t)tid < t1 - t0;
-        const uint32_t bi = bb + c;
-        const unsigned long long fg = own ? a.seam_cut[2 * (size_t)bi] : NONE;
-        const unsigned long long lg = own ? a.seam_cut[2 * (size_t)bi + 1] : NONE;
-        KMax v = kmax_none();
-        if (fg != NONE) { v.k = ~fg; v.tb = 0; v.valid = 1; }
-        const KMax ex = kmax(carry, block_excl_max(v, ks, &tot));
-        if (lg != NONE) emit(lg, ex.valid ? ~ex.k : n);
+        const uint32_t t0 = t1 > PST ? t1 - PST : 0;
+        unsigned long long fg[PSI], lg[PSI];
+        KMax loc = kmax_none();
+#pragma unroll
+        for (int k = 0; k < PSI; ++k) {
+            const uint32_t r = (uint32_t)tid * PSI + k;
+            const bool own = r < t1 - t0;
+            const uint32_t bi = bb + (t1 - 1 - r);
+            fg[k] = own ? a.seam_cut[2 * (size_t)bi] : NONE;
+            lg[k] = own ? a.seam_cut[2 * (size_t)bi + 1] : NONE;
+            if (fg[k] != NONE) {
+                KMax v; v.k = ~fg[k]; v.tb = 0; v.valid = 1;
+                loc = kmax(loc, v);
+            }
+        }
+        KMax run = kmax(carry, block_excl_max(loc, ks, &tot));
+#pragma unroll
+        for (int k = 0; k < PSI; ++k) {
+            if (lg[k] != NONE) emit(lg[k], run.valid ? ~run.k : n);
+            if (fg[k] != NONE) {
+                KMax v; v.k = ~fg[k]; v.tb = 0; v.valid = 1;
+                run = kmax(run, v);
+            }
+        }
         carry = kmax(carry, tot);
         t1 = t0;
     }
