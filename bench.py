@@ -41,7 +41,7 @@ WORKLOAD = ("268,435,456 float32 keys lognormal(0,2) with 5% exact duplicates, k
 # DRAM bytes per key of one launch, from the ncu captures summarised under profiles/ (2^26 keys,
 # same distribution and model recipe; traffic grows in proportion to the keys)
 TRAFFIC_PER_KEY = {
-    ("predict", "bf16x2"): 7.380,   # profiles/k_predict_bf16_split_64M.md
+    ("predict", "bf16x2"): 7.365,   # profiles/k_predict_bf16_mg_split_64M.md
     ("rounds", None): 6.805,        # profiles/k_rounds_64M.md
     ("polish", None): 12.657,       # profiles/k_polish_64M.md
     ("partition", None): 15.566,    # profiles/k_onesweep_partition_64M.md (per pass)
@@ -580,7 +580,7 @@ def main():
         # bound by the binary32 work on the CUDA cores around the tensor-core layer
         ach = n * CUDA_CORE_FLOP_PER_KEY[precision] / (dom_ms / 1e3) / 1e12
         tens = n * 2 * 64 * 64 * (2 if precision == "bf16x2" else 1) / (dom_ms / 1e3) / 1e12
-        roof = {"kernel": "predict (k_predict_bf16)", "bound": "alu", "achieved": ach,
+        roof = {"kernel": "predict (k_predict_bf16_mg)", "bound": "alu", "achieved": ach,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
                 "tensor": {"achieved": tens, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
