@@ -85,6 +85,34 @@ def test_injected_positions_match_oracle(n):
                         payload=np.arange(n, dtype=np.int32))
 
 
+@pytest.mark.parametrize("kind", ["few_distinct", "far_outliers", "spread", "u64_spread"])
+def test_bucket_sort_paths(kind):
+    """Each bucket is sorted whole: by one counting pass over bins of its key range, or by radix
+    sort when a bin crowds (few distinct keys, or a few far outliers that stretch the range).
+    Positions follow the key order (buckets of ~3,300 keys at 4,096 positions), with noise."""
+    n = 300_000
+    rs = np.random.RandomState(11)
+    if kind == "few_distinct":
+        keys = rs.randint(0, 40, n).astype(np.float32)
+    elif kind == "far_outliers":
+        keys = W.uniform_f32(n, 12)
+        far = rs.rand(n) < 0.002
+        keys[far] = np.float32(3.0e38)
+    elif kind == "spread":
+        keys = W.lognormal_dup_f32(n, 13, sigma=2.0)
+    else:
+        keys = W.uniform_u64(n, 14)
+    L, _, _ = orc.nm_split(n)
+    rank = np.argsort(np.argsort(keys, kind="stable"), kind="stable")
+    slots = np.clip((rank * 1.25 + rs.randint(-40, 41, n)).astype(np.int64), 0, L - 1)
+    if kind == "far_outliers":  # the outliers land in random buckets and stretch their key range
+        slots[far] = rs.randint(0, L, int(far.sum()))
+    payload = np.arange(n, dtype=np.int32)
+    for eps in (1, 3):
+        _check_injected(keys, slots.astype(np.uint32), L, eps, 0, payload=payload, bucket_log2=12)
+        _check_injected(keys, slots.astype(np.uint32), L, eps, 0, bucket_log2=12)
+
+
 def test_injected_degenerate_maps():
     n = 20_000
     keys = W.uniform_f32(n, 9)
