@@ -264,13 +264,13 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
     auto lpos = [&](uint32_t i) -> uint32_t { return onchip ? (uint32_t)pos[i] : (a.gs[s0 + i] & wm); };
     // Algorithm NN-sort: in iteration r every element still unplaced claims its position; the
     // lowest row (first arrival) is stored, the others move on to the next conflict array
-    const unsigned lanes_below = (1u << (tid & 31)) - 1u;
     for (int r = 0; r < eps; ++r) {
         for (uint32_t j = tid; j < Wn; j += RT) tbl[j] = EMPTY32;
         __syncthreads();
-        // lanes of a warp hold consecutive rows: among lanes claiming the same position only the
-        // lowest can win, so only it issues the atomic (positions crowd when f is coarse). Loads are
-        // issued LB at a time (the round index and position may live in global memory).
+        // every claimant issues a shared-memory atomicMin of its row (the lowest row wins); a warp
+        // match to let only the lowest lane of a position claim cost more than the atomics it saved,
+        // except where nearly every key shares a few positions. Loads are issued LB at a time (the
+        // round index and position may live in global memory).
         for (uint32_t i0 = 0; i0 < nbk; i0 += RT * LB) {
             uint32_t pv[LB];
 #pragma unroll
@@ -281,8 +281,7 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
 #pragma unroll
             for (int q = 0; q < LB; ++q) {
                 const uint32_t i = i0 + q * RT + tid;
-                const unsigned peers = __match_any_sync(0xFFFFFFFFu, pv[q]);
-                if (pv[q] != EMPTY32 && (peers & lanes_below) == 0) atomicMin(&tbl[pv[q]], i);
+                if (pv[q] != EMPTY32) atomicMin(&tbl[pv[q]], i);
             }
         }
         __syncthreads();
@@ -367,22 +366,36 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_finalize(SolveArgs a) {
     __syncthreads();
     const int t = sh_t;
     const uint32_t nb = sg.nb, bb = sg.bbase;
-    const uint32_t per = (nb + SOLVE_THREADS - 1) / SOLVE_THREADS;
-    const uint32_t c0 = std::min(nb, tid * per), c1 = std::min(nb, c0 + per);
+    // tiles of PSI * SOLVE_THREADS buckets, PSI consecutive ones per thread
+    constexpr int PSI = 8;
+    constexpr uint32_t PST = SOLVE_THREADS * PSI;
+    __shared__ KMax tot;
     for (int r = 0; r < t; ++r) {
-        KMax loc = kmax_none();
-        for (uint32_t c = c0; c < c1; ++c) {
-            const OKey o = a.bmax[(size_t)(bb + c) * MAXR + r];
-            KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid;
-            loc = kmax(loc, x);
-        }
-        KMax run = block_excl_max(loc, scratch, nullptr);
-        for (uint32_t c = c0; c < c1; ++c) {
-            OKey co; co.k = run.k; co.tb = run.tb; co.valid = run.valid;
-            a.carry[(size_t)(bb + c) * MAXR + r] = co;
-            const OKey o = a.bmax[(size_t)(bb + c) * MAXR + r];
-            KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid;
-            run = kmax(run, x);
+        KMax carry = kmax_none();  // maximum stored in o_r by the buckets before the tile
+        for (uint32_t t0 = 0; t0 < nb; t0 += PST) {
+            KMax v[PSI];
+            KMax loc = kmax_none();
+#pragma unroll
+            for (int k = 0; k < PSI; ++k) {
+                const uint32_t c = t0 + (uint32_t)tid * PSI + k;
+                v[k] = kmax_none();
+                if (c < nb) {
+                    const OKey o = a.bmax[(size_t)(bb + c) * MAXR + r];
+                    v[k].k = o.k; v[k].tb = o.tb; v[k].valid = o.valid;
+                }
+                loc = kmax(loc, v[k]);
+            }
+            KMax run = kmax(carry, block_excl_max(loc, scratch, &tot));
+#pragma unroll
+            for (int k = 0; k < PSI; ++k) {
+                const uint32_t c = t0 + (uint32_t)tid * PSI + k;
+                if (c < nb) {
+                    OKey co; co.k = run.k; co.tb = run.tb; co.valid = run.valid;
+                    a.carry[(size_t)(bb + c) * MAXR + r] = co;
+                }
+                run = kmax(run, v[k]);
+            }
+            carry = kmax(carry, tot);
         }
     }
 }
@@ -909,10 +922,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_ps(SolveArgs a) {
 #pragma unroll
         for (int k = 0; k < PSI; ++k) {  // this thread's buckets, later ones first
             const uint32_t r = (uint32_t)tid * PSI + k;
-            const uint32_t bi = bb + (t1 - 1 - r);
-            const bool ne = r < t1 - t0 && a.bstart[bi + 1] > a.bstart[bi];
+            const bool own = r < t1 - t0;
+            const uint32_t bi = bb + (own ? t1 - 1 - r : 0u);
+            // bounds and key read together; the key of an empty bucket is read but not used
+            const uint32_t s0 = a.bstart[bi], s1 = a.bstart[bi + 1];
+            const OKey o = a.blo[bi];
+            const bool ne = own && s1 > s0;
             nem |= (ne ? 1u : 0u) << k;
-            v[k] = ne ? kinv(okey(a.blo[bi])) : kmax_none();
+            v[k] = ne ? kinv(okey(o)) : kmax_none();
             loc = kmax(loc, v[k]);
         }
         KMax run = kmax(carry, block_excl_max(loc, ks, &tot));
@@ -936,10 +953,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_ps(SolveArgs a) {
 #pragma unroll
         for (int k = 0; k < PSI; ++k) {
             const uint32_t c = t0 + (uint32_t)tid * PSI + k;
-            const uint32_t bi = bb + c;
-            const bool ne = c < nb && a.bstart[bi + 1] > a.bstart[bi];
+            const bool own = c < nb;
+            const uint32_t bi = bb + (own ? c : 0u);
+            const uint32_t s0 = a.bstart[bi], s1 = a.bstart[bi + 1];
+            const OKey o = a.bhi[bi];
+            const bool ne = own && s1 > s0;
             nem |= (ne ? 1u : 0u) << k;
-            v[k] = ne ? okey(a.bhi[bi]) : kmax_none();
+            v[k] = ne ? okey(o) : kmax_none();
             loc = kmax(loc, v[k]);
         }
         KMax run = kmax(carry, block_excl_max(loc, ks, &tot));
