@@ -112,11 +112,22 @@ def tuned_entry(dtype: int, n: int, layers: int, h1: int, h2: int, precision: st
     return t[min(cands)[1]] if cands else None
 
 
+PRECISIONS = ("fp32", "bf16x2", "bf16", "pwl")
+
+
 def tuned_options(dtype: int, n: int, layers: int, h1: int, h2: int, precision: str,
                   path: str = TABLE) -> dict:
-    """Tuned keyword arguments for sort()/sort_batch(); the nearest table entry of the same key
-    type, model shape and precision when n's class was not tuned, else the library defaults."""
+    """Tuned keyword arguments for sort()/sort_batch(): the nearest table entry of the same key
+    type, model shape and precision; when that precision was never tuned for the class, the entry
+    of another precision of the same key type and model shape (bucket width, polish blocks and
+    round limit depend on the data and the model far more than on the form of the forward pass);
+    else the library defaults."""
     e = tuned_entry(dtype, n, layers, h1, h2, precision, path)
+    for other in PRECISIONS:
+        if e is not None:
+            break
+        if other != precision:
+            e = tuned_entry(dtype, n, layers, h1, h2, other, path)
     if e is None:
         return dict(DEFAULTS)
     return {k: e[k] for k in DEFAULTS if k in e}

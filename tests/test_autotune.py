@@ -53,8 +53,15 @@ def test_table_round_trip_and_fallbacks(tmp_path):
     # nearest size class of the same key type, shape and precision
     assert AT.tuned_options(0, 1 << 26, 2, 64, 64, "bf16", path=path)["bucket_log2"] == 11
     assert AT.tuned_options(0, 1 << 22, 2, 64, 64, "bf16", path=path)["bucket_log2"] == 10
-    # another precision, shape or key type has no entry
-    assert AT.tuned_options(0, 1 << 28, 2, 64, 64, "fp32", path=path) == AT.DEFAULTS
+    # a precision never tuned for this key type and shape takes another precision's entry
+    assert AT.tuned_options(0, 1 << 28, 2, 64, 64, "fp32", path=path) == \
+        {"bucket_log2": 11, "polish_blocks": 2, "eps": 2}
+    assert AT.tuned_entry(0, 1 << 28, 2, 64, 64, "fp32", path=path) is None
+    # but an entry of the requested precision wins, whatever its size class
+    AT.save_entry(AT.table_key(0, 1 << 20, 2, 64, 64, "pwl"),
+                  {"bucket_log2": 13, "polish_blocks": 1, "eps": 4}, 2.0, path)
+    assert AT.tuned_options(0, 1 << 28, 2, 64, 64, "pwl", path=path)["bucket_log2"] == 13
+    # another shape or key type has no entry
     assert AT.tuned_options(0, 1 << 28, 1, 64, 0, "bf16", path=path) == AT.DEFAULTS
     assert AT.tuned_options(1, 1 << 28, 2, 64, 64, "bf16", path=path) == AT.DEFAULTS
 
