@@ -284,7 +284,6 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
     extern __shared__ __align__(16) float sm[];
     float *sp = sm, *W2T = sm + S::OFF_W2T, *sH1 = sm + S::OFF_H1, *sH2 = sm + S::OFF_H2;
     float *sD2 = sm + S::OFF_D2, *sD1 = sm + S::OFF_D1, *sX = sm + S::OFF_X, *sGY = sm + S::OFF_GY;
-    float *sL = sm + S::OFF_L;
     const int tid = threadIdx.x;
     for (int i = tid; i < P; i += TR_THREADS) sp[i] = g.params[i];
     __syncthreads();
@@ -308,8 +307,15 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
     for (int i = 0; i < TK; ++i)
 #pragma unroll
         for (int q = 0; q < TP; ++q) aW2[i][q] = 0ull;
-    float aV = 0.0f, aV2 = 0.0f;  // per-thread vector gradients (see the role split below)
-    float lacc = 0.0f;
+    // vector gradients as per-thread partial sums, combined in a fixed order after the last chunk:
+    // the D2 pass gives thread t the fixed column t % H (db2, dW3) over every (TR_THREADS / H)-th
+    // sample; the D1 product's epilogue gives it columns n0..n0+TN-1 over rows m0..m0+3 (db1, dW1);
+    // threads t < GC see sample t of every chunk (db3, loss)
+    static_assert(TR_THREADS % H == 0, "fixed D2 column per thread");
+    float pb2 = 0.0f, pw3 = 0.0f, pgy = 0.0f, plv = 0.0f;
+    float pb1[TN], pw1[TN];
+#pragma unroll
+    for (int q = 0; q < TN; ++q) { pb1[q] = 0.0f; pw1[q] = 0.0f; }
     const uint64_t per = (g.n + gridDim.x - 1) / gridDim.x;
     const uint64_t i0 = std::min<uint64_t>(g.n, (uint64_t)blockIdx.x * per);
     const uint64_t i1 = std::min<uint64_t>(g.n, i0 + per);
@@ -383,12 +389,17 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
                 }
             }
             sGY[tid] = gy;
-            sL[tid] = lv;
+            pgy = __fadd_rn(pgy, gy);
+            plv = __fadd_rn(plv, lv);
         }
         __syncthreads();
         for (int e = tid; e < GC * H; e += TR_THREADS) {
-            const int s = e / H, k = e % H;
-            sD2[s * LD + k] = (sH2[s * LD + k] > 0.0f) ? sGY[s] * W3[k] : 0.0f;
+            const int s = e / H, k = e % H;  // k = tid % H on every iteration
+            const float h2 = sH2[s * LD + k];
+            const float d = (h2 > 0.0f) ? sGY[s] * W3[k] : 0.0f;
+            sD2[s * LD + k] = d;
+            pb2 = __fadd_rn(pb2, d);
+            pw3 = __fmaf_rn(sGY[s], h2, pw3);
         }
         __syncthreads();
         {   // D1 = [H1 > 0] (D2 W2)
@@ -417,8 +428,14 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
                     float d0, d1;
                     upk2(acc[i][q], d0, d1);
                     const int c = (m0 + i) * LD + n0 + 2 * q;
-                    sD1[c] = (sH1[c] > 0.0f) ? d0 : 0.0f;
-                    sD1[c + 1] = (sH1[c + 1] > 0.0f) ? d1 : 0.0f;
+                    const float e0 = (sH1[c] > 0.0f) ? d0 : 0.0f, e1 = (sH1[c + 1] > 0.0f) ? d1 : 0.0f;
+                    sD1[c] = e0;
+                    sD1[c + 1] = e1;
+                    const float xs = sX[m0 + i];
+                    pb1[2 * q] = __fadd_rn(pb1[2 * q], e0);
+                    pb1[2 * q + 1] = __fadd_rn(pb1[2 * q + 1], e1);
+                    pw1[2 * q] = __fmaf_rn(e0, xs, pw1[2 * q]);
+                    pw1[2 * q + 1] = __fmaf_rn(e1, xs, pw1[2 * q + 1]);
                 }
         }
         __syncthreads();
@@ -441,25 +458,18 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
                 for (int q = 0; q < TP; ++q) aW2[i][q] = fma2_rn(a2, b[q], aW2[i][q]);
             }
         }
-        // vectors: t < H -> (db2_t, dW3_t); H <= t < 2H -> (db1_j, dW1_j); t == 2H -> db3
-        if (tid < H) {
-            for (int s = 0; s < cn; ++s) {
-                aV = __fadd_rn(aV, sD2[s * LD + tid]);
-                aV2 = __fmaf_rn(sGY[s], sH2[s * LD + tid], aV2);
-            }
-        } else if (tid < 2 * H) {
-            const int j = tid - H;
-            for (int s = 0; s < cn; ++s) {
-                aV = __fadd_rn(aV, sD1[s * LD + j]);
-                aV2 = __fmaf_rn(sD1[s * LD + j], sX[s], aV2);
-            }
-        } else if (tid == 2 * H) {
-            for (int s = 0; s < cn; ++s) aV = __fadd_rn(aV, sGY[s]);
-        }
-        if (tid == TR_THREADS - 1)
-            for (int s = 0; s < cn; ++s) lacc = __fadd_rn(lacc, sL[s]);
         __syncthreads();
     }
+    // combine the partial sums (the activation tiles are free now)
+    float *R2b = sH1, *R2w = R2b + TR_THREADS, *R1b = R2w + TR_THREADS, *R1w = R1b + TR_THREADS * TN;
+    float *Rg = R1w + TR_THREADS * TN, *Rl = Rg + GC;
+    static_assert((2 + 2 * TN) * TR_THREADS + 2 * GC <= 4 * GC * LD, "partials fit the activation tiles");
+    R2b[tid] = pb2;
+    R2w[tid] = pw3;
+#pragma unroll
+    for (int q = 0; q < TN; ++q) { R1b[tid * TN + q] = pb1[q]; R1w[tid * TN + q] = pw1[q]; }
+    if (tid < GC) { Rg[tid] = pgy; Rl[tid] = plv; }
+    __syncthreads();
     float *out = g.partials + (size_t)blockIdx.x * P;
 #pragma unroll
     for (int i = 0; i < TK; ++i)
@@ -470,16 +480,32 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
             out[2 * H + (k0 + i) * H + j0 + 2 * q] = w0;
             out[2 * H + (k0 + i) * H + j0 + 2 * q + 1] = w1;
         }
-    if (tid < H) {
-        out[2 * H + H * H + tid] = aV;       // b2
-        out[3 * H + H * H + tid] = aV2;      // W3
-    } else if (tid < 2 * H) {
-        out[H + (tid - H)] = aV;             // b1
-        out[tid - H] = aV2;                  // W1
+    if (tid < H) {  // column tid of D2: threads tid, tid + H, ...
+        float b = 0.0f, w = 0.0f;
+        for (int ph = 0; ph < TR_THREADS / H; ++ph) {
+            b = __fadd_rn(b, R2b[ph * H + tid]);
+            w = __fadd_rn(w, R2w[ph * H + tid]);
+        }
+        out[2 * H + H * H + tid] = b;        // b2
+        out[3 * H + H * H + tid] = w;        // W3
+    } else if (tid < 2 * H) {  // column j of D1: thread (tm, j / TN), slot j % TN, for every tm
+        const int j = tid - H, tn = j / TN, q = j % TN;
+        float b = 0.0f, w = 0.0f;
+        for (int tm2 = 0; tm2 < TR_THREADS / 16; ++tm2) {
+            b = __fadd_rn(b, R1b[(tm2 * 16 + tn) * TN + q]);
+            w = __fadd_rn(w, R1w[(tm2 * 16 + tn) * TN + q]);
+        }
+        out[H + j] = b;                      // b1
+        out[j] = w;                          // W1
     } else if (tid == 2 * H) {
-        out[P - 1] = aV;                     // b3
+        float b = 0.0f;
+        for (int t2 = 0; t2 < GC; ++t2) b = __fadd_rn(b, Rg[t2]);
+        out[P - 1] = b;                      // b3
+    } else if (tid == 2 * H + 1 && g.loss_partials) {
+        float l = 0.0f;
+        for (int t2 = 0; t2 < GC; ++t2) l = __fadd_rn(l, Rl[t2]);
+        g.loss_partials[blockIdx.x] = l;
     }
-    if (tid == TR_THREADS - 1 && g.loss_partials) g.loss_partials[blockIdx.x] = lacc;
 }
 
 template <int H1, int H2> static size_t grad_smem() {
