@@ -8,7 +8,7 @@
 // One pass reads and writes each element once. A tile ranks its elements per digit stably (a warp
 // finds the lanes holding the same digit from one ballot per digit bit, then counts them with popc),
 // publishes its per-digit counts, and learns its global offsets by decoupled look-back over earlier
-// tiles, four at a time (tiles are numbered by an atomic ticket, so every tile waited on has already
+// tiles, eight at a time (tiles are numbered by an atomic ticket, so every tile waited on has already
 // started). Writes go out through a shared-memory reorder buffer in digit order, so each digit's
 // run leaves as coalesced stores.
 #include <algorithm>
@@ -135,10 +135,10 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
             st_release_u64(lb, lb_pack(a.epoch, FLAG_INCL, total));
         } else {
             st_release_u64(lb, lb_pack(a.epoch, FLAG_AGG, total));
-            // four predecessors per round trip: their words are read together (each word carries
+            // eight predecessors per round trip: their words are read together (each word carries
             // its own flag and value, so no ordering between them is needed), then taken in order
             // until an inclusive prefix ends the walk or a tile that has not published stops it
-            constexpr int LBW = 4;
+            constexpr int LBW = 8;
             long long p = (long long)tile - 1;
             unsigned long long t0 = 0;
             bool done = false;

@@ -37,6 +37,7 @@ namespace nns {
 
 constexpr int SOLVE_THREADS = 512;
 constexpr int SNW = SOLVE_THREADS / 32;
+constexpr int SCAN_THREADS = 1024;  // one block per array for the scans over its buckets
 
 __device__ __forceinline__ int seg_of_bucket(const Seg *segs, int nseg, uint32_t b) {
     int lo = 0, hi = nseg - 1;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
 
 // ---------------------------------------------------------------------------------------------
 // k_finalize: one block per array
-__global__ void __launch_bounds__(SOLVE_THREADS) k_finalize(SolveArgs a) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_finalize(SolveArgs a) {
     __shared__ KMax scratch[33];
     __shared__ int sh_t;
     const int s = blockIdx.x, tid = threadIdx.x;
@@ -366,9 +367,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_finalize(SolveArgs a) {
     __syncthreads();
     const int t = sh_t;
     const uint32_t nb = sg.nb, bb = sg.bbase;
-    // tiles of PSI * SOLVE_THREADS buckets, PSI consecutive ones per thread
+    // tiles of PSI * SCAN_THREADS buckets, PSI consecutive ones per thread
     constexpr int PSI = 8;
-    constexpr uint32_t PST = SOLVE_THREADS * PSI;
+    constexpr uint32_t PST = SCAN_THREADS * PSI;
     __shared__ KMax tot;
     for (int r = 0; r < t; ++r) {
         KMax carry = kmax_none();  // maximum stored in o_r by the buckets before the tile
@@ -901,11 +902,11 @@ __device__ __forceinline__ KMax kinv(const KMax &x) {
 // t the bucket tile_end - 1 - t, so that an exclusive scan over threads runs over later buckets.
 // 1) k_seam_ps (one block per array): S(b) = the smallest element of the buckets after b,
 //    P(b) = the largest element of the buckets before b.
-__global__ void __launch_bounds__(SOLVE_THREADS) k_seam_ps(SolveArgs a) {
-    // tiles of PSI * SOLVE_THREADS buckets, PSI consecutive ones per thread: a thread folds its own
+__global__ void __launch_bounds__(SCAN_THREADS) k_seam_ps(SolveArgs a) {
+    // tiles of PSI * SCAN_THREADS buckets, PSI consecutive ones per thread: a thread folds its own
     // buckets in order and one block scan per tile carries the rest
     constexpr int PSI = 8;
-    constexpr uint32_t PST = SOLVE_THREADS * PSI;
+    constexpr uint32_t PST = SCAN_THREADS * PSI;
     __shared__ KMax ks[33];
     __shared__ KMax tot;
     const int s = blockIdx.x, tid = threadIdx.x;
@@ -1262,7 +1263,7 @@ cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s) {
-    k_finalize<<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
+    k_finalize<<<a.nseg, SCAN_THREADS, 0, s>>>(a);
     return nns_launched(cudaGetLastError());
 }
 
@@ -1281,7 +1282,7 @@ cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s) {
 template <typename W> static cudaError_t seam_go(const SolveArgs &a, int sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.seam_cnt, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_seam_ps<<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
+    k_seam_ps<<<a.nseg, SCAN_THREADS, 0, s>>>(a);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
     k_seam_cuts<W><<<(a.NB + 255) / 256, 256, 0, s>>>(a);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
