@@ -9,7 +9,7 @@
  * CUDA path.
  *
  * What each part follows:
- *   - translate(A): Sec. "Input Phase" (line 1 of Fig. "Algorithm NN-sort"): keys are encoded as
+ *   - translate(A): Sec. "Input Phase" (the translate step of Fig. "Algorithm NN-sort"): keys are encoded as
  *     model inputs; numeric keys are min-max normalised with the training sample's range.
  *   - the model f and its training: Sec. "Training" and Sec. "Experimental Study / Training details"
  *     (regression MLP, rounding to a position, Adam; Huber loss of Eq. (loss)).

@@ -1,5 +1,5 @@
-// k_predict.cu -- lines 1 and 5-7 of Fig. "Algorithm NN-sort": w <- translate(A),
-// w_pos <- w.map(f), pos <- round(w_pos * m), for every key, in binary32.
+// k_predict.cu -- the translate, map and rounding steps of Fig. "Algorithm NN-sort":
+// w <- translate(A), w_pos <- w.map(f), pos <- round(w_pos * m), for every key, in binary32.
 //
 // One pass over the keys (128-bit friendly striped loads), the model's parameters staged once per
 // block in shared memory, the position written as a global position gs = gs_base + pos, and the

@@ -4,7 +4,7 @@
 // [b W, (b+1) W) of one array) are contiguous and in input order. Because every element keeps
 // its position in every iteration (same f, same scale), the paper's iterations decompose over
 // buckets exactly:
-//   k_rounds   -- Fig. "Algorithm NN-sort" lines 3-14 inside one bucket: each iteration clears
+//   k_rounds   -- the iteration loop of Fig. "Algorithm NN-sort" inside one bucket: each iteration clears
 //                 o_i, lets every still-unplaced element claim its position (the first to arrive,
 //                 i.e. the lowest input row, wins -- "only the first element is stored"), and sends
 //                 the others on to the next conflict array. Output: the iteration in which each
@@ -15,8 +15,10 @@
 //   k_polish   -- Fig. "Algorithm polish" inside one bucket: o_i's stored elements in position
 //                 order; an element smaller than the largest earlier element of o_i (carry from
 //                 earlier buckets included) is out of order and joins the leftover, the rest form
-//                 a sorted run R_i; the last conflict array plus the out-of-order elements are
-//                 sorted (radix sort by key, stable); A' <- merge(A', R_i) for i = 1..t.
+//                 a sorted run R_i (this gives the out-of-order counts and fates). The result of
+//                 sorting the leftover and merging it with R_1..R_t is the bucket's elements in
+//                 (key, row) order, so the bucket is sorted whole (a counting pass over bins of
+//                 its key range, or a stable radix sort by key where bins crowd).
 //   k_seam     -- the buckets' outputs are each sorted; where a non-monotone f lets a later
 //                 bucket hold a key smaller than an earlier bucket's, the affected range is
 //                 located and re-sorted (the polish Remark: out-of-order elements end up at their
@@ -570,25 +572,6 @@ __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_
     }
     __syncthreads();
     return src;
-}
-
-// merge two lists sorted under `less` (a strict total order) into C; caller synchronises
-template <typename Idx, typename Less>
-__device__ void cta_merge(const Idx *A, uint32_t na, const Idx *B, uint32_t nb, Idx *C, Less less) {
-    const uint32_t total = na + nb;
-    const uint32_t per = (total + SOLVE_THREADS - 1) / SOLVE_THREADS;
-    const uint32_t d0 = std::min(total, threadIdx.x * per), d1 = std::min(total, d0 + per);
-    if (d0 >= d1) return;
-    uint32_t lo = d0 > nb ? d0 - nb : 0, hi = std::min(d0, na);
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (less(B[d0 - 1 - mid], A[mid])) hi = mid; else lo = mid + 1;
-    }
-    uint32_t i = lo, j = d0 - lo;
-    for (uint32_t q = d0; q < d1; ++q) {
-        if (j >= nb || (i < na && less(A[i], B[j]))) C[q] = A[i++];
-        else C[q] = B[j++];
-    }
 }
 
 // ---------------------------------------------------------------------------------------------
