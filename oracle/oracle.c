@@ -4,7 +4,7 @@
  *  arXiv 1907.08817).
  *
  * TEST INFRASTRUCTURE ONLY. The product library never links, loads or calls this file. Only the
- * test-suite, the smoke check and the CPU-baseline leg of the benchmark use it, as the checker the
+ * test-suite, the smoke check and the CPU-baseline leg of the benchmark use it, as the reference the
  * CUDA path is compared against. It shares no code, header, table or constant generator with the
  * CUDA path.
  *
@@ -604,7 +604,7 @@ static int cmp_rows(const void *pa, const void *pb) {
     return 0;
 }
 
-/* The leftover sort ("QuickSort(w)") and the checker sort: rows by (key, row). */
+/* The leftover sort ("QuickSort(w)") and the reference sort: rows by (key, row). */
 void orc_sort_rows(const void *keys, int dtype, uint32_t *rows, uint64_t cnt) {
     g_sort_ctx.keys = keys;
     g_sort_ctx.dtype = dtype;
@@ -738,7 +738,7 @@ int orc_nnsort_model(const void *keys, int dtype, const int32_t *payload, uint64
     return rc;
 }
 
-/* Checker: the stable sort of the input by (key, row). */
+/* Reference: the stable sort of the input by (key, row). */
 void orc_stable_sort(const void *keys, int dtype, const int32_t *payload, uint64_t n, void *out_keys,
                      int32_t *out_payload) {
     uint32_t *rows = (uint32_t *)malloc((n + 1) * sizeof(uint32_t));
