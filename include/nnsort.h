@@ -178,6 +178,14 @@ int nnsort_release(void);
 /* Device-side error word raised by kernels on `stream` since the last call that read it
  * (NNSORT_OK, NNSORT_E_NAN_KEY, NNSORT_E_TIMEOUT or NNSORT_E_INVALID_ARG); synchronises. */
 int nnsort_stream_status(cudaStream_t stream);
+/* Self-test of the timeout path shared by every device-side wait in the library: one thread waits
+ * on a device flag that nothing sets, polling %globaltimer with the library's wait loop, for
+ * limit_us microseconds (clamped to [1, 1,000,000]) or a fixed number of polls, then raises the
+ * timeout bit of a device error word and returns. Returns NNSORT_E_TIMEOUT when the wait expired
+ * as it must (NNSORT_OK would mean the flag was seen set). Nothing faults, traps or hangs; the
+ * context stays usable. Synchronous; uses two words of static device memory, so concurrent calls
+ * must not overlap. */
+int nnsort_selftest_wait(uint32_t limit_us, cudaStream_t stream);
 /* Number of kernels the library has launched in this process (all devices and streams). */
 uint64_t nnsort_launch_count(void);
 /* Bytes of device workspace a sort of n keys of `dtype` (payload or not) uses. */

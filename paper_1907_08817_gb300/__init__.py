@@ -43,6 +43,12 @@ def stream_status(stream=None) -> int:
     return int(L.lib().nnsort_stream_status(_stream(stream)))
 
 
+def selftest_wait(limit_us: int = 1000, stream=None) -> int:
+    """Runs the library's bounded device-side wait on a flag that nothing sets; the status is
+    NNSORT_E_TIMEOUT (-6) when the wait expired as it must."""
+    return int(L.lib().nnsort_selftest_wait(int(limit_us), _stream(stream)))
+
+
 def key_code(t, key_type: str | None = None) -> int:
     """nnsort_dtype of a key tensor/array. int32/int64 storage holds unsigned keys' bits and needs
     key_type='u32'/'u64'."""

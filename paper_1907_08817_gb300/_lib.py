@@ -95,6 +95,7 @@ def lib():
         "nnsort_default_sort_opts": (None, [P]),
         "nnsort_release": (C.c_int, []),
         "nnsort_stream_status": (C.c_int, [P]),
+        "nnsort_selftest_wait": (C.c_int, [C.c_uint32, P]),
         "nnsort_workspace_bytes": (sz, [u64, i32, i32, P]),
         "nnsort_model_create": (C.c_int, [P, P, P]),
         "nnsort_model_free": (C.c_int, [P]),
@@ -133,7 +134,8 @@ def exported_symbols() -> list[str]:
     """Every entry point name the binding declares (the header's declarations)."""
     return ["nnsort_version", "nnsort_strerror", "nnsort_last_cuda_error",
             "nnsort_default_train_opts", "nnsort_default_sort_opts", "nnsort_release",
-            "nnsort_stream_status", "nnsort_workspace_bytes", "nnsort_model_create",
+            "nnsort_stream_status", "nnsort_selftest_wait", "nnsort_workspace_bytes",
+            "nnsort_model_create",
             "nnsort_model_free", "nnsort_model_describe", "nnsort_model_blob_size",
             "nnsort_model_save", "nnsort_model_load", "nnsort_mlp_pwl", "nnsort_sample_labels",
             "nnsort_train",

@@ -419,6 +419,44 @@ int nnsort_model_load(const void *h_blob, size_t size, nnsort_model **out) {
     return nnsort_model_create(&d, params.data(), out);
 }
 
+}  // extern "C"
+
+namespace {
+__device__ uint32_t g_selftest_flag;  // never set
+__device__ uint32_t g_selftest_err;
+
+__global__ void k_selftest_wait(unsigned long long limit_ns) {
+    const volatile uint32_t *flag = &g_selftest_flag;
+    const unsigned long long t0 = nns::globaltimer_ns();
+    uint32_t polls = 0;
+    while (*flag == 0u) {
+        if (nns::globaltimer_ns() - t0 > limit_ns || ++polls > nns::SPIN_LIMIT_POLLS) {
+            atomicOr(&g_selftest_err, nns::ERR_TIMEOUT);
+            return;
+        }
+        __nanosleep(256);
+    }
+}
+}  // namespace
+
+extern "C" {
+
+int nnsort_selftest_wait(uint32_t limit_us, cudaStream_t stream) {
+    const uint32_t us = limit_us < 1u ? 1u : (limit_us > 1000000u ? 1000000u : limit_us);
+    void *pf = nullptr, *pe = nullptr;
+    CK(cudaGetSymbolAddress(&pf, g_selftest_flag));
+    CK(cudaGetSymbolAddress(&pe, g_selftest_err));
+    CK(cudaMemsetAsync(pf, 0, sizeof(uint32_t), stream));
+    CK(cudaMemsetAsync(pe, 0, sizeof(uint32_t), stream));
+    k_selftest_wait<<<1, 1, 0, stream>>>((unsigned long long)us * 1000ull);
+    CK(cudaGetLastError());
+    nns::note_launch(1);
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, pe, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return (e & nns::ERR_TIMEOUT) ? NNSORT_E_TIMEOUT : NNSORT_OK;
+}
+
 int nnsort_stream_status(cudaStream_t s) {
     Workspace *w = nullptr;
     int rc = get_ws(s, &w);

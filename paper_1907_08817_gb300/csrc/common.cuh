@@ -211,8 +211,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// every spin-wait in the library gives up after this long and raises ERR_TIMEOUT
+// every spin-wait in the library gives up after this long, or after this many polls (whichever
+// comes first, so that a wait ends even if the timer were not to advance), and raises ERR_TIMEOUT
 constexpr unsigned long long SPIN_LIMIT_NS = 4000000000ull;
+constexpr uint32_t SPIN_LIMIT_POLLS = 1u << 26;
 
 // ---------------------------------------------------------------------------------------------
 // block-wide exclusive sum of one u32 per thread (blockDim multiple of 32, <= 1024)

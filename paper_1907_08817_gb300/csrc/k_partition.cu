@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
             constexpr int LBW = 8;
             long long p = (long long)tile - 1;
             unsigned long long t0 = 0;
+            uint32_t polls = 0;
             bool done = false;
             while (!done) {
                 unsigned long long v[LBW];
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
                 if (used) continue;
                 const unsigned long long now = globaltimer_ns();
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > SPIN_LIMIT_NS) {
+                else if (now - t0 > SPIN_LIMIT_NS || ++polls > SPIN_LIMIT_POLLS) {
                     atomicOr(a.err, ERR_TIMEOUT);
                     break;
                 }

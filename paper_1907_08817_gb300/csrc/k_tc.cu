@@ -75,8 +75,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // bounded wait: false when the limit expired
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     const unsigned long long t0 = globaltimer_ns();
+    uint32_t polls = 0;
     while (!mbar_try(bar, parity)) {
-        if (globaltimer_ns() - t0 > SPIN_LIMIT_NS) return false;
+        if (globaltimer_ns() - t0 > SPIN_LIMIT_NS || ++polls > SPIN_LIMIT_POLLS) return false;
     }
     return true;
 }
