@@ -78,10 +78,25 @@ class Clocks:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        # the sampler takes a moment to start: let its first row arrive (at most 3 s) so that the
+        # timed region that follows is sampled
+        t0 = time.perf_counter()
+        while self.p is not None and self.p.poll() is None and time.perf_counter() - t0 < 3.0:
+            try:
+                if os.path.getsize(self.f.name) > 0:
+                    break
+            except OSError:
+                break
+            time.sleep(0.01)
+        self.skip = 0
+        try:
+            self.skip = len([r for r in open(self.f.name).read().splitlines() if r.strip()])
+        except OSError:
+            pass
         return self
 
     def __exit__(self, *a):
@@ -97,6 +112,9 @@ class Clocks:
             rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
         except Exception:
             rows = []
+        # rows logged before the timed region opened are not counted, unless there is nothing else
+        if len(rows) > getattr(self, "skip", 0):
+            rows = rows[getattr(self, "skip", 0):]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
