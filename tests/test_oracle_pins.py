@@ -84,6 +84,93 @@ def test_mlp_forward_closed_form():
                                atol=1e-6)
 
 
+def test_mlp_layer1_closed_form():
+    """Hidden layer 1 alone, h[i][j] = relu(W1_j x_i + b1_j), row-major [n][h1], against the
+    expression written out on hand-set weights (n != h1, so a transposed layout fails)."""
+    W1 = [1.0, -2.0, 0.5]; b1 = [0.0, 1.0, -0.25]
+    p = np.array(W1 + b1 + [1.0, 1.0, 1.0, 0.0], dtype=np.float32)
+    x = np.array([-1.0, 0.0, 0.25, 0.5, 2.0], dtype=np.float32)
+    h = O.mlp_layer1_f32(1, 3, 0, p, x)
+    assert h.shape == (5, 3)
+    want = [[max(w * v + b, 0.0) for w, b in zip(W1, b1)] for v in x.tolist()]
+    assert h.tolist() == want
+    # a two-hidden-layer parameter vector starts with the same W1, b1 block
+    p2 = np.concatenate([p[:6], np.ones(3 * 2 + 2 + 2 + 1, np.float32)])
+    assert p2.shape[0] == O.num_params(2, 3, 2)
+    assert O.mlp_layer1_f32(2, 3, 2, p2, x).tolist() == want
+    # one rounding per unit (a fused multiply-add): w = x = 1 + 2^-12, b = -1 gives exactly
+    # 2^-11 + 2^-24, which a rounded product followed by a rounded sum would lose
+    e = 2.0 ** -12
+    p1 = np.array([1 + e, -1.0, 1.0, 0.0], dtype=np.float32)
+    got = O.mlp_layer1_f32(1, 1, 0, p1, np.array([1 + e], np.float32))[0, 0]
+    exact = Fraction(1 + e) * Fraction(1 + e) - 1
+    assert Fraction(float(got)) == exact == Fraction(1, 2 ** 11) + Fraction(1, 2 ** 24)
+
+
+def _init_blocks(p, layers, h1, h2):
+    W1, b1 = p[:h1], p[h1:2 * h1]
+    if layers == 2:
+        W2 = p[2 * h1:2 * h1 + h2 * h1]
+        b2 = p[2 * h1 + h2 * h1:2 * h1 + h2 * h1 + h2]
+        W3 = p[2 * h1 + h2 * h1 + h2:-1]
+    else:
+        W2, b2, W3 = None, None, p[2 * h1:-1]
+    return W1, b1, W2, b2, W3, p[-1]
+
+
+def test_init_params_draws_ranges_and_layout():
+    """Initialisation (Sec. Experimental Study, training details; the recipe of the first layer's
+    kinks is this library's reading): stream (seed, tag 2) of SplitMix64 drawn in the order W1, kink
+    positions, W2 (row-major [h2][h1]), W3. Pinned by the generator's independent numpy form,
+    by the ranges and moments of the uniform laws (a wrong He range or fan-in fails them) and by
+    the kink placement b1_j = -W1_j c_j with c_j in [0, 1)."""
+    seed = 5
+    s = W.stream_seed(seed, 2)
+    layers, h1, h2 = 2, 16, 64
+    p = O.init_params(layers, h1, h2, seed)
+    W1, b1, W2, b2, W3, b3 = _init_blocks(p, layers, h1, h2)
+    d = W.rng_u64(s, 0, 2 * h1 + h2 * h1 + h2)
+    u = (d >> np.uint64(11)).astype(np.float64) / 2.0 ** 53
+    # the first draws mapped by hand: W1_0 = (2u_0 - 1) sqrt 6, b1_0 = -W1_0 u_h1
+    assert W1[0] == np.float32((2 * u[0] - 1) * math.sqrt(6))
+    assert b1[0] == np.float32(-float(W1[0]) * u[h1])
+    np.testing.assert_array_equal(W1, ((2 * u[:h1] - 1) * math.sqrt(6)).astype(np.float32))
+    np.testing.assert_array_equal(b1, (-W1.astype(np.float64) * u[h1:2 * h1]).astype(np.float32))
+    np.testing.assert_array_equal(
+        W2, ((2 * u[2 * h1:2 * h1 + h2 * h1] - 1) * math.sqrt(6 / h1)).astype(np.float32))
+    np.testing.assert_array_equal(W3, ((2 * u[2 * h1 + h2 * h1:] - 1) * math.sqrt(6 / h2))
+                                  .astype(np.float32))
+    assert np.all(b2 == 0) and b3 == 0
+    # ranges: W2's fan-in is h1 = 16, W3's is h2 = 64 (a fan-out or sqrt(6 fan_in) range fails)
+    for w, r in ((W1, math.sqrt(6)), (W2, math.sqrt(6 / h1)), (W3, math.sqrt(6 / h2))):
+        assert np.all(np.abs(w) <= np.float32(r))
+    assert np.abs(W2).max() > 0.95 * math.sqrt(6 / h1)
+    assert np.abs(W3).max() > 0.8 * math.sqrt(6 / h2)
+    # moments of U(-r, r): mean 0, variance r^2 / 3 (1,024 draws of W2)
+    assert abs(W2.mean()) < 0.05 * math.sqrt(6 / h1)
+    assert abs(W2.astype(np.float64).var() / (2 / h1) - 1) < 0.15
+    # every kink -b1_j / W1_j lies in the unit input range
+    c = -b1.astype(np.float64) / W1.astype(np.float64)
+    assert np.all((c >= -1e-7) & (c < 1 + 1e-7))
+
+
+def test_init_params_first_layer_statistics_and_seeds():
+    h1 = 256
+    p = O.init_params(1, h1, 0, 11)
+    W1, b1, _, _, W3, b3 = _init_blocks(p, 1, h1, 0)
+    assert np.abs(W1).max() > 0.9 * math.sqrt(6) and np.all(np.abs(W1) <= np.float32(math.sqrt(6)))
+    assert abs(W1.astype(np.float64).var() / 2.0 - 1) < 0.3
+    c = -b1.astype(np.float64) / W1.astype(np.float64)
+    assert np.all((c >= -1e-7) & (c < 1 + 1e-7))
+    assert abs(c.mean() - 0.5) < 0.1 and c.min() < 0.05 and c.max() > 0.95
+    # one hidden layer: the output weights' fan-in is h1
+    assert np.all(np.abs(W3) <= np.float32(math.sqrt(6 / h1)))
+    assert np.abs(W3).max() > 0.9 * math.sqrt(6 / h1) and b3 == 0
+    # deterministic per seed, different across seeds
+    np.testing.assert_array_equal(p, O.init_params(1, h1, 0, 11))
+    assert not np.array_equal(p, O.init_params(1, h1, 0, 12))
+
+
 def test_mlp_forward_f32_tracks_f64():
     for layers, h1, h2 in ((1, 32, 0), (2, 16, 16), (2, 64, 64)):
         p = O.init_params(layers, h1, h2, 7)
