@@ -161,15 +161,6 @@ void nns::note_launch(int kernels) { g_launches.fetch_add((unsigned long long)ke
 
 // ---------------------------------------------------------------------------------------------
 // models
-struct nnsort_model {
-    nnsort_model_desc desc;
-    std::vector<float> params;  // caller layout
-    PadArch pad;
-    size_t P = 0, Ppad = 0;
-    float *d_params = nullptr;  // padded layout
-    int device = 0;
-};
-
 namespace nns {
 PadArch pad_arch(int layers, int h1, int h2) {
     auto up = [](int h) { return h <= 8 ? 8 : h <= 16 ? 16 : h <= 32 ? 32 : 64; };

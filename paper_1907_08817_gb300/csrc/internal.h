@@ -235,3 +235,14 @@ cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, 
                                    cudaStream_t s);
 
 }  // namespace nns
+
+// The model handle behind the opaque nnsort_model of the C ABI: one definition for every
+// translation unit that reads it.
+struct nnsort_model {
+    nnsort_model_desc desc;
+    std::vector<float> params;  // caller layout
+    nns::PadArch pad;
+    size_t P = 0, Ppad = 0;
+    float *d_params = nullptr;  // padded layout
+    int device = 0;
+};

@@ -20,16 +20,6 @@
 
 using namespace nns;
 
-// the model handle as the library defines it (api.cu)
-struct nnsort_model {
-    nnsort_model_desc desc;
-    std::vector<float> params;
-    PadArch pad;
-    size_t P = 0, Ppad = 0;
-    float *d_params = nullptr;
-    int device = 0;
-};
-
 namespace {
 
 constexpr uint64_t NA_MAX_N = NNSORT_NOALLOC_MAX_N;
@@ -142,8 +132,11 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     if (n == 0) return NNSORT_OK;
     if (!d_keys) return NNSORT_E_INVALID_ARG;
 
-    // host scalar set-up of the paper's definitions (same as nnsort_sort)
+    // host scalar set-up of the paper's definitions (same as nnsort_sort); the position count
+    // L = floor(n m) + 1 must fit the fixed bucket tables before anything is narrowed
     const double nm = (double)n * (double)o.m;
+    if (!std::isfinite(nm) || std::floor(nm) + 1.0 > (double)((uint64_t)NA_MAX_BUCKETS << wlog))
+        return NNSORT_E_INVALID_ARG;
     Seg sg;
     std::memset(&sg, 0, sizeof(sg));
     sg.keys = d_keys;
@@ -202,6 +195,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     pa.err = L.err;
     pa.key_bytes = kb;
     pa.dtype = dtype;
+    pa.single_model = 1;  // one array whose positions come from its model, as in nnsort_sort
     int sms = 1;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     {
