@@ -121,3 +121,28 @@ def test_split_bf16_resolves_f_like_binary32():
         distinct[prec] = int(torch.unique(y).numel())
     assert distinct["bf16x2"] >= 0.9 * distinct["fp32"]
     assert distinct["bf16x2"] > 2 * distinct["bf16"]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+def test_batched_tensor_core_forms_match_the_oracle_given_single_array_positions(prec):
+    """Arrays of a batch, each with its own 1-64-64-1 model, run through the batched tensor-core
+    kernel (one W2 per array, reloaded when a block's sub-tile changes array). Its positions equal
+    the single-array kernel's for the same model (same per-row arithmetic), so every array's output,
+    payload and per-round counts must equal the oracle's procedure given those positions."""
+    arrs = [a for _, a in W.batch_arrays(7, seed=44, lo=20_000, hi=150_000)]
+    models, slots = [], []
+    for j, a in enumerate(arrs):
+        om, _, _ = orc.train(a, 2, 64, 64, orc.ORDBITS, sample_n=1000, steps=20, seed=j)
+        f = lib_model(om)
+        models.append(f)
+        s, _ = nns.predict(to_dev(a)[0], f, precision=prec, want_y=False)
+        slots.append(s.cpu().numpy().astype(np.uint32))
+    dks = [to_dev(a)[0] for a in arrs]
+    dps = [torch.arange(a.shape[0], dtype=torch.int32, device="cuda") for a in arrs]
+    sts = nns.sort_batch(dks, models, dps, precision=prec, eps=3, bucket_log2=12, polish_blocks=2)
+    for a, s, dk, dp, st in zip(arrs, slots, dks, dps, sts):
+        L, _, _ = orc.nm_split(a.shape[0])
+        ok, op, ost, _ = orc.nnsort(a, s, L, 3, 1024, np.arange(a.shape[0], dtype=np.int32))
+        np.testing.assert_array_equal(bits(from_dev(dk, a)), bits(ok))
+        np.testing.assert_array_equal(dp.cpu().numpy(), op)
+        assert stats_core(st) == stats_core(ost)
