@@ -26,6 +26,9 @@ Workloads (the paper's Experimental Study uses uniform, normal and lognormal 64-
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import os
+
 import numpy as np
 
 GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -65,11 +68,25 @@ def _normal_f64(seed: int, start: int, count: int) -> np.ndarray:
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 
+def _threads() -> int:
+    return max(1, min(32, os.cpu_count() or 1))
+
+
 def _chunked(n: int, fn, dtype) -> np.ndarray:
+    """fn(start, count) for consecutive chunks of [0, n); chunks are independent (counter-based
+    draws), so they are computed on a thread pool (numpy releases the GIL) with the same result."""
     out = np.empty(n, dtype=dtype)
-    for s in range(0, n, _CHUNK):
+
+    def one(s):
         c = min(_CHUNK, n - s)
         out[s:s + c] = fn(s, c)
+    starts = range(0, n, _CHUNK)
+    if n <= _CHUNK or _threads() == 1:
+        for s in starts:
+            one(s)
+    else:
+        with cf.ThreadPoolExecutor(_threads()) as ex:
+            list(ex.map(one, starts))
     return out
 
 
@@ -168,15 +185,17 @@ def batch_arrays(count: int = 4096, seed: int = 4, lo: int = 1000, hi: int = 1_0
     u = _unit_f64(rng_u64(stream_seed(seed, 1), 0, count))
     sizes = np.floor(lo * (hi / lo) ** u).astype(np.int64)
     kinds = (rng_u64(stream_seed(seed, 2), 0, count) % np.uint64(len(_DISTS))).astype(np.int64)
-    out = []
-    total = 0
-    for j in range(count):
-        if total_cap is not None and total + int(sizes[j]) > total_cap:
-            break
-        out.append((_DISTS[kinds[j]], dist_f32(_DISTS[kinds[j]], int(sizes[j]),
-                                               stream_seed(seed, 100 + j))))
-        total += int(sizes[j])
-    return out
+    take = count
+    if total_cap is not None:
+        csum = np.cumsum(sizes)
+        take = int(np.searchsorted(csum, total_cap, side="right"))
+
+    def one(j):
+        return (_DISTS[kinds[j]], dist_f32(_DISTS[kinds[j]], int(sizes[j]), stream_seed(seed, 100 + j)))
+    if take > 8 and _threads() > 1:
+        with cf.ThreadPoolExecutor(_threads()) as ex:
+            return list(ex.map(one, range(take)))
+    return [one(j) for j in range(take)]
 
 
 def serving_requests(count: int = 1000, seed: int = 5, lo: int = 10_000, hi: int = 16_000_000,
