@@ -272,6 +272,15 @@ int nnsort_train_sort_host(void *h_keys, int32_t *h_payload, uint64_t n, int32_t
 int nnsort_sort_batch(void *const *d_keys, int32_t *const *d_payloads, const uint64_t *ns,
                       int32_t count, int32_t dtype, const nnsort_model *const *fs,
                       const nnsort_sort_opts *o, nnsort_stats *st, cudaStream_t stream);
+/* The "no model" reference of the ablation in Sec. "Experimental Study" (what the learned part
+ * gains is measured against sorting without it): a stable LSD radix sort of d_keys[n] (and
+ * d_payload[n], nullable) by the keys' order images (8-bit digits; -0.0 before +0.0), every pass
+ * the same partition kernel the NN-sort pipeline uses for its buckets. In place, caller-owned
+ * device arrays; scratch from the stream's workspace. Synchronous. Errors: NNSORT_E_INVALID_ARG
+ * (bad dtype, null keys with n > 0, n >= 2^32 - 1), NNSORT_E_OOM, NNSORT_E_CUDA,
+ * NNSORT_E_TIMEOUT (a bounded device wait expired). */
+int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtype,
+                      cudaStream_t stream);
 
 /* ---- serving: continuous batching of sort requests ------------------------------------ */
 /* A server owns `workers` CUDA streams on the current device and a host scheduler thread.

@@ -15,7 +15,7 @@ from . import _lib as L
 from ._lib import (F32, F64, U32, U64, ORDBITS, VALUE, PREC_BF16, PREC_FP32, LOSS_HUBER,
                    LOSS_MSE, NNSortError)
 
-__all__ = ["Model", "train", "sample_labels", "predict", "sort", "sort_batch", "sort_host",
+__all__ = ["Model", "train", "sample_labels", "predict", "sort", "sort_batch", "sort_host", "radix_sort",
            "mlp_forward", "mlp_backward", "mlp_loss_grad", "NNSortMLPFunction", "NNSortError",
            "key_code", "release", "workspace_bytes", "stream_status", "version"]
 
@@ -251,6 +251,13 @@ def sort(keys, payload=None, model: Model | None = None, *, m=1.25, eps=3, tau=1
     L.check("nnsort_sort", rc)
     out = st.as_dict() if st is not None else None
     return (out, ft) if fate else out
+
+
+def radix_sort(keys, payload=None, *, key_type=None, stream=None) -> None:
+    """The "no model" reference: stable LSD radix sort of the keys (and payload) in place, every
+    pass the pipeline's partition kernel (nnsort_radix_sort)."""
+    L.check("nnsort_radix_sort", L.lib().nnsort_radix_sort(
+        _ptr(keys), _ptr(payload), keys.numel(), key_code(keys, key_type), _stream(stream)))
 
 
 def sort_host(keys: np.ndarray, payload: np.ndarray | None = None, model: Model | None = None, *,

@@ -1106,6 +1106,67 @@ int nnsort_sort_batch(void *const *d_keys, int32_t *const *d_payloads, const uin
     return run_sort(in, o, dtype, st, stream);
 }
 
+int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtype, cudaStream_t s) {
+    if (!dtype_ok(dtype) || n >= 0xFFFFFFFFull) return NNSORT_E_INVALID_ARG;
+    if (n == 0) return NNSORT_OK;
+    if (!d_keys) return NNSORT_E_INVALID_ARG;
+    Workspace *w = nullptr;
+    int rc = get_ws(s, &w);
+    if (rc) return rc;
+    const int kb = key_bytes_of(dtype);
+    const bool pay = d_payload != nullptr;
+    Carve c;
+    auto layout = [&](unsigned char *base) {
+        c = Carve();
+        c.base = base;
+        struct { uint32_t *err, *hist, *bases, *tickets; void *k1; uint32_t *p1; } r;
+        r.err = c.take<uint32_t>(4);
+        r.hist = c.take<uint32_t>(8 * RADIX_BINS);
+        r.bases = c.take<uint32_t>(8 * RADIX_BINS);
+        r.tickets = c.take<uint32_t>(8 * 4);
+        r.k1 = c.take<unsigned char>(n * kb);
+        r.p1 = pay ? c.take<uint32_t>(n) : nullptr;
+        return r;
+    };
+    layout(nullptr);
+    if ((rc = ensure_arena(w, c.off, s))) return rc;
+    const uint64_t tiles = (n + PART_TILE - 1) / PART_TILE;
+    if ((rc = ensure_lookback(w, tiles * RADIX_BINS, s))) return rc;
+    auto L = layout(w->arena);
+    w->last_err = L.err;
+    CK(cudaMemsetAsync(L.err, 0, 16, s));
+    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
+    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
+    const int npass = kb;  // 8-bit digits; an even count, so the result ends in the caller's arrays
+    CK(launch_key_hist(d_keys, n, kb, dtype, npass, L.hist, s));
+    CK(launch_digit_bases(L.hist, L.bases, npass, s));
+    void *K[2] = {d_keys, L.k1};
+    uint32_t *P[2] = {reinterpret_cast<uint32_t *>(d_payload), L.p1};
+    for (int p = 0; p < npass; ++p) {
+        const int si = p & 1, di = si ^ 1;
+        OnesweepArgs a{};
+        a.N = n;
+        a.key_in = K[si];
+        a.key_out = K[di];
+        if (pay) { a.pay_in = P[si]; a.pay_out = P[di]; }
+        a.key_digits = 1;
+        a.shift = 8 * p;
+        a.bits = 8;
+        a.digit_base = L.bases + p * RADIX_BINS;
+        a.lookback = w->lookback;
+        a.ticket = L.tickets + p * 4;
+        a.epoch = next_epoch(w, s);
+        a.err = L.err;
+        a.key_bytes = kb;
+        a.dtype = dtype;
+        CK(launch_onesweep(a, s));
+    }
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(&err, L.err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return (err & ERR_TIMEOUT) ? NNSORT_E_TIMEOUT : NNSORT_OK;
+}
+
 int nnsort_sort_host(void *h_keys, int32_t *h_payload, uint64_t n, int32_t dtype, const nnsort_model *f,
                      const nnsort_sort_opts *o, nnsort_stats *st, cudaStream_t stream) {
     if (!dtype_ok(dtype) || (n && !h_keys)) return NNSORT_E_INVALID_ARG;

@@ -448,3 +448,27 @@ def test_giant_buckets_sorted_multi_block():
     np.testing.assert_array_equal(dp.cpu().numpy(), op)
     assert stats_core(st) == stats_core(ost)
     assert st["oversized_buckets"] >= 1
+
+
+# ---------------------------------------------------------------------------- no-model reference
+def test_radix_sort_reference_is_the_stable_sort():
+    """nnsort_radix_sort (the ablation's "no model" reference: every pass the partition kernel on
+    8-bit key digits) gives the stable order by (key, row): keys bit-exact, payload = stable
+    permutation, for f32 (signed zeros, infinities, duplicates, a ragged tail), f64 and u64."""
+    rs = np.random.RandomState(77)
+    f = W.lognormal_dup_f32(300_001, 5, sigma=2.0)
+    f[:6] = [-0.0, 0.0, np.inf, -np.inf, -1.5, 0.0]
+    cases = [f, rs.standard_normal(123_457), (rs.randint(0, 2 ** 63, 200_003, dtype=np.int64)
+                                              .astype(np.uint64) * np.uint64(2))]
+    for keys in cases:
+        payload = np.arange(keys.shape[0], dtype=np.int32)
+        dk, kt = to_dev(keys)
+        dp = torch.from_numpy(payload).cuda()
+        nns.radix_sort(dk, dp, key_type=kt)
+        ok, op = orc.stable_sort(keys, payload)
+        np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+        np.testing.assert_array_equal(dp.cpu().numpy(), op)
+        dk, kt = to_dev(keys)
+        nns.radix_sort(dk, None, key_type=kt)  # keys only
+        np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    nns.radix_sort(torch.empty(0, device="cuda"))
