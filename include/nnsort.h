@@ -278,7 +278,7 @@ int nnsort_sort_batch(void *const *d_keys, int32_t *const *d_payloads, const uin
  * the same partition kernel the NN-sort pipeline uses for its buckets. In place, caller-owned
  * device arrays; scratch from the stream's workspace. Synchronous. Errors: NNSORT_E_INVALID_ARG
  * (bad dtype, null keys with n > 0, n >= 2^32 - 1), NNSORT_E_OOM, NNSORT_E_CUDA,
- * NNSORT_E_TIMEOUT (a bounded device wait expired). */
+ * NNSORT_E_TIMEOUT (reserved: the partition passes hold no device-side waits). */
 int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtype,
                       cudaStream_t stream);
 
@@ -334,9 +334,8 @@ int nnsort_server_destroy(nnsort_server *srv);
  *   - n may be at most NNSORT_NOALLOC_MAX_N, and floor(n m) + 1 at most 1024 buckets of
  *     2^bucket_log2 positions; larger requests return NNSORT_E_INVALID_ARG and touch nothing.
  *   - f is required (o->d_slots and o->d_fate must be NULL).
- *   - The first call on a device looks up the scratch's device address and clears its look-back
- *     area (cudaGetSymbolAddress, cudaMemsetAsync); make that first call before any stream
- *     capture.
+ *   - The first call on a device looks up the scratch's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture.
  *   - Every call shares the one scratch array and finds the previous call's contents there; each
  *     call clears what must start at zero. Calls whose work overlaps on the GPU (for example on
  *     two streams at once) race on the scratch and must be serialised by the caller.

@@ -53,9 +53,8 @@ struct Workspace {
     int device = -1;
     unsigned char *arena = nullptr;
     size_t cap = 0;
-    unsigned long long *lookback = nullptr;
-    size_t lb_cap = 0;  // entries
-    uint32_t epoch = 0;
+    unsigned char *part = nullptr;  // partition scratch: tile histograms, then chunk bases
+    size_t part_cap = 0;
     unsigned char *pinned = nullptr;
     size_t pcap = 0;
     uint32_t *last_err = nullptr;  // device error word of the last sort on this stream
@@ -115,32 +114,32 @@ int ensure_pinned(Workspace *w, size_t bytes, cudaStream_t s) {
     return NNSORT_OK;
 }
 
-int ensure_lookback(Workspace *w, size_t entries, cudaStream_t s) {
-    if (entries > w->lb_cap) {
-        CK(cudaStreamSynchronize(s));
-        if (w->lookback) CK(cudaFree(w->lookback));
-        w->lookback = nullptr;
-        const size_t want = align_up(entries + entries / 4, 1 << 16);
-        cudaError_t e = cudaMalloc(&w->lookback, want * sizeof(unsigned long long));
-        if (e != cudaSuccess) {
-            g_last_cuda = (int)e;
-            cudaGetLastError();
-            w->lb_cap = 0;
-            return NNSORT_E_OOM;
-        }
-        w->lb_cap = want;
-        CK(cudaMemsetAsync(w->lookback, 0, want * sizeof(unsigned long long), s));
-        w->epoch = 0;
+size_t part_hist_bytes(uint64_t N) { return align_up(partition_tiles(N) * RADIX_BINS * sizeof(uint16_t), 256); }
+
+// scratch of the partition passes over up to N elements
+int ensure_part(Workspace *w, uint64_t N, cudaStream_t s) {
+    const size_t bytes = part_hist_bytes(N) + partition_chunks(N) * RADIX_BINS * sizeof(uint32_t);
+    if (bytes <= w->part_cap) return NNSORT_OK;
+    CK(cudaStreamSynchronize(s));
+    if (w->part) CK(cudaFree(w->part));
+    w->part = nullptr;
+    w->part_cap = 0;
+    const size_t want = align_up(bytes + bytes / 4, 1 << 16);
+    cudaError_t e = cudaMalloc(&w->part, want);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        cudaGetLastError();
+        return NNSORT_E_OOM;
     }
+    w->part_cap = want;
     return NNSORT_OK;
 }
 
-uint32_t next_epoch(Workspace *w, cudaStream_t s) {
-    if (++w->epoch >= 0xFFFFu) {
-        cudaMemsetAsync(w->lookback, 0, w->lb_cap * sizeof(unsigned long long), s);
-        w->epoch = 1;
-    }
-    return w->epoch;
+// one partition pass over N elements with the workspace's scratch
+cudaError_t part_pass(Workspace *w, PartitionArgs a, cudaStream_t s) {
+    a.tile_hist = reinterpret_cast<uint16_t *>(w->part);
+    a.chunk = reinterpret_cast<uint32_t *>(w->part + part_hist_bytes(a.N));
+    return launch_partition(a, s);
 }
 
 // bump allocator over the arena
@@ -317,7 +316,7 @@ int nnsort_release(void) {
         cudaSetDevice(w->device);
         cudaDeviceSynchronize();
         if (w->arena) cudaFree(w->arena);
-        if (w->lookback) cudaFree(w->lookback);
+        if (w->part) cudaFree(w->part);
         if (w->pinned) cudaFreeHost(w->pinned);
         if (w->host_dev) cudaFree(w->host_dev);
         delete w;
@@ -476,7 +475,7 @@ struct SegIn {
 };
 
 struct Layout {
-    Seg *segs; SegStats *stats; uint32_t *err; uint32_t *hist; uint32_t *bases; uint32_t *tickets;
+    Seg *segs; SegStats *stats; uint32_t *err; uint32_t *hist; uint32_t *bases;
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2]; uint32_t *row[2]; uint32_t *out_rows;
     uint8_t *rank; uint8_t *g_flag; uint32_t *g_x, *g_y; uint32_t *bstart;
     OKey *bmax, *carry, *blo, *bhi;
@@ -496,7 +495,6 @@ Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, boo
     L.err = c.take<uint32_t>(4);
     L.hist = c.take<uint32_t>(8 * RADIX_BINS);
     L.bases = c.take<uint32_t>(8 * RADIX_BINS);
-    L.tickets = c.take<uint32_t>(8 * 4);
     for (int i = 0; i < 2; ++i) {
         L.gs[i] = c.take<uint32_t>(N);
         L.key[i] = c.take<unsigned char>(N * kb);
@@ -640,7 +638,7 @@ int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void
                 cudaStream_t s) {
     auto pass = [&](int p, int si, bool keydig, int shift, int bits, const uint32_t *base) -> int {
         const int di = si ^ 1;
-        OnesweepArgs a{};
+        PartitionArgs a{};
         a.N = total;
         a.key_in = K[si];
         a.key_out = K[di];
@@ -658,19 +656,14 @@ int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void
         a.shift = shift;
         a.bits = bits;
         a.digit_base = base;
-        a.lookback = w->lookback;
-        a.ticket = L.tickets + p * 4;
-        a.epoch = next_epoch(w, s);
-        a.err = L.err;
         a.key_bytes = kb;
         a.dtype = dtype;
-        CK(launch_onesweep(a, s));
+        CK(part_pass(w, a, s));
         return NNSORT_OK;
     };
     int rc;
     const int npass = kb;  // even, so the key passes end in pair 0
     CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
-    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
     CK(launch_key_hist(K[0], total, kb, dtype, npass, L.hist, s));
     CK(launch_digit_bases(L.hist, L.bases, npass, s));
     for (int p = 0; p < npass; ++p)
@@ -692,7 +685,6 @@ int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void
                 hp[q * RADIX_BINS + ((gl.first >> sh[q]) & ((1u << bt[q]) - 1u))] += (uint32_t)gl.second;
         }
         CK(cudaMemcpyAsync(L.hist, hp, sizeof(uint32_t) * nsp * RADIX_BINS, cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
         CK(launch_digit_bases(L.hist, L.bases, nsp, s));
         for (int q = 0; q < nsp; ++q)
             if ((rc = pass(q, q & 1, false, sh[q], bt[q], L.bases + q * RADIX_BINS))) return rc;
@@ -803,8 +795,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     Workspace *w = nullptr;
     if ((rc = get_ws(s, &w))) return rc;
     if ((rc = ensure_arena(w, pwl_off + pwl_bytes, s))) return rc;
-    const uint64_t ptiles = (P.N + PART_TILE - 1) / PART_TILE;
-    if ((rc = ensure_lookback(w, ptiles * RADIX_BINS, s))) return rc;
+    if ((rc = ensure_part(w, P.N, s))) return rc;
     // staging: the segment table, then the statistics, the seam counters and the long seam ranges
     // (disjoint and longer than SEAM_CTA_MAX each, so at most N / SEAM_CTA_MAX of them)
     const size_t pin_stats = align_up(sizeof(Seg) * nseg, 64);
@@ -836,7 +827,6 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     CK(cudaMemsetAsync(L.stats, 0, sizeof(SegStats) * nseg, s));
     CK(cudaMemsetAsync(L.err, 0, 16, s));
     CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * MAX_PASSES * RADIX_BINS, s));
-    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * MAX_PASSES * 4, s));
 
     const bool timing = o.timing && st;
     if (timing && !w->ev[0])
@@ -870,7 +860,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     CK(launch_digit_bases(L.hist, L.bases, P.pp.npass, s));
     for (int p = 0; p < P.pp.npass; ++p) {
         const int si = p & 1, di = si ^ 1;
-        OnesweepArgs a{};
+        PartitionArgs a{};
         a.N = P.N;
         a.gs_in = L.gs[si];
         a.gs_out = L.gs[di];
@@ -885,13 +875,9 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
         a.shift = P.pp.shift[p];
         a.bits = P.pp.bits[p];
         a.digit_base = L.bases + p * RADIX_BINS;
-        a.lookback = w->lookback;
-        a.ticket = L.tickets + p * 4;
-        a.epoch = next_epoch(w, s);
-        a.err = L.err;
         a.key_bytes = kb;
         a.dtype = dtype;
-        CK(launch_onesweep(a, s));
+        CK(part_pass(w, a, s));
     }
     const int fi = P.pp.npass & 1, oi = fi ^ 1;
     CK(mark(2));
@@ -1045,7 +1031,7 @@ size_t nnsort_workspace_bytes(uint64_t n, int32_t dtype, int32_t with_payload, c
     size_t need = 0;
     const bool rows = o.d_fate != nullptr || (o.d_slots != nullptr && with_payload);
     carve(nullptr, 1, n, P.NB, key_bytes_of(dtype), with_payload != 0, rows, &need);
-    return need + ((n + PART_TILE - 1) / PART_TILE) * RADIX_BINS * sizeof(unsigned long long);
+    return need + part_hist_bytes(n) + partition_chunks(n) * RADIX_BINS * sizeof(uint32_t);
 }
 
 int nnsort_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtype, const nnsort_model *f,
@@ -1119,24 +1105,21 @@ int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtyp
     auto layout = [&](unsigned char *base) {
         c = Carve();
         c.base = base;
-        struct { uint32_t *err, *hist, *bases, *tickets; void *k1; uint32_t *p1; } r;
+        struct { uint32_t *err, *hist, *bases; void *k1; uint32_t *p1; } r;
         r.err = c.take<uint32_t>(4);
         r.hist = c.take<uint32_t>(8 * RADIX_BINS);
         r.bases = c.take<uint32_t>(8 * RADIX_BINS);
-        r.tickets = c.take<uint32_t>(8 * 4);
         r.k1 = c.take<unsigned char>(n * kb);
         r.p1 = pay ? c.take<uint32_t>(n) : nullptr;
         return r;
     };
     layout(nullptr);
     if ((rc = ensure_arena(w, c.off, s))) return rc;
-    const uint64_t tiles = (n + PART_TILE - 1) / PART_TILE;
-    if ((rc = ensure_lookback(w, tiles * RADIX_BINS, s))) return rc;
+    if ((rc = ensure_part(w, n, s))) return rc;
     auto L = layout(w->arena);
     w->last_err = L.err;
     CK(cudaMemsetAsync(L.err, 0, 16, s));
     CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
-    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
     const int npass = kb;  // 8-bit digits; an even count, so the result ends in the caller's arrays
     CK(launch_key_hist(d_keys, n, kb, dtype, npass, L.hist, s));
     CK(launch_digit_bases(L.hist, L.bases, npass, s));
@@ -1144,7 +1127,7 @@ int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtyp
     uint32_t *P[2] = {reinterpret_cast<uint32_t *>(d_payload), L.p1};
     for (int p = 0; p < npass; ++p) {
         const int si = p & 1, di = si ^ 1;
-        OnesweepArgs a{};
+        PartitionArgs a{};
         a.N = n;
         a.key_in = K[si];
         a.key_out = K[di];
@@ -1153,13 +1136,9 @@ int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtyp
         a.shift = 8 * p;
         a.bits = 8;
         a.digit_base = L.bases + p * RADIX_BINS;
-        a.lookback = w->lookback;
-        a.ticket = L.tickets + p * 4;
-        a.epoch = next_epoch(w, s);
-        a.err = L.err;
         a.key_bytes = kb;
         a.dtype = dtype;
-        CK(launch_onesweep(a, s));
+        CK(part_pass(w, a, s));
     }
     uint32_t err = 0;
     CK(cudaMemcpyAsync(&err, L.err, 4, cudaMemcpyDeviceToHost, s));
@@ -1275,33 +1254,30 @@ int nnsort_sample_labels(const void *d_keys, uint64_t n, int32_t dtype, uint64_t
     auto lay = [&](unsigned char *base) {
         c = Carve();
         c.base = base;
-        struct { void *k[2]; uint32_t *r[2]; uint32_t *hist, *bases, *tickets, *err; Norm *norm; } L;
+        struct { void *k[2]; uint32_t *r[2]; uint32_t *hist, *bases, *err; Norm *norm; } L;
         L.k[0] = c.take<unsigned char>(S * kb);
         L.k[1] = c.take<unsigned char>(S * kb);
         L.r[0] = c.take<uint32_t>(S);
         L.r[1] = c.take<uint32_t>(S);
         L.hist = c.take<uint32_t>(8 * RADIX_BINS);
         L.bases = c.take<uint32_t>(8 * RADIX_BINS);
-        L.tickets = c.take<uint32_t>(8 * 4);
-        L.err = c.take<uint32_t>(4);
+            L.err = c.take<uint32_t>(4);
         L.norm = c.take<Norm>(1);
         return L;
     };
     lay(nullptr);
     if ((rc = ensure_arena(w, c.off + 1024, s))) return rc;
     auto L = lay(w->arena);
-    const uint64_t tiles = (S + PART_TILE - 1) / PART_TILE;
-    if ((rc = ensure_lookback(w, tiles * RADIX_BINS, s))) return rc;
+    if ((rc = ensure_part(w, S, s))) return rc;
     if ((rc = ensure_pinned(w, 256, s))) return rc;
     CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
-    CK(cudaMemsetAsync(L.tickets, 0, sizeof(uint32_t) * 8 * 4, s));
     CK(cudaMemsetAsync(L.err, 0, 16, s));
     CK(launch_sample(d_keys, n, kb, dtype, S, rng_h(seed, TAG_SAMPLE), L.k[0], L.r[0], L.err, s));
     CK(launch_key_hist(L.k[0], S, kb, dtype, npass, L.hist, s));
     CK(launch_digit_bases(L.hist, L.bases, npass, s));
     for (int p = 0; p < npass; ++p) {
         const int si = p & 1, di = si ^ 1;
-        OnesweepArgs a{};
+        PartitionArgs a{};
         a.N = S;
         a.key_in = L.k[si];
         a.key_out = L.k[di];
@@ -1311,13 +1287,9 @@ int nnsort_sample_labels(const void *d_keys, uint64_t n, int32_t dtype, uint64_t
         a.shift = 8 * p;
         a.bits = 8;
         a.digit_base = L.bases + p * RADIX_BINS;
-        a.lookback = w->lookback;
-        a.ticket = L.tickets + p * 4;
-        a.epoch = next_epoch(w, s);
-        a.err = L.err;
         a.key_bytes = kb;
         a.dtype = dtype;
-        CK(launch_onesweep(a, s));
+        CK(part_pass(w, a, s));
     }
     const int fi = npass & 1;  // even pass count -> result back in buffer 0
     // extremes of the sorted sample -> normaliser (host scalar set-up)

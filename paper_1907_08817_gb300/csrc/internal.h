@@ -18,9 +18,6 @@ struct OKey;
 
 constexpr int RADIX_MAX_BITS = 9;
 constexpr int RADIX_BINS = 1 << RADIX_MAX_BITS;  // 512
-constexpr int PART_THREADS = 512;
-constexpr int PART_ITEMS = 16;
-constexpr int PART_TILE = PART_THREADS * PART_ITEMS;  // 8192
 constexpr int PRED_THREADS = 256;
 constexpr int PRED_ITEMS = 8;
 constexpr int PRED_TILE = PRED_THREADS * PRED_ITEMS;  // 2048
@@ -84,7 +81,16 @@ void pwl_key_table(const nnsort_model_desc &d, const std::vector<double> &brk, c
                    const std::vector<double> &icept, double nm, PwlEntry *out);
 
 // ---- partition (k_partition.cu)
-struct OnesweepArgs {
+// One pass of the stable digit partition without inter-block waits (reduce, then scan, then
+// scatter): per tile of SC_TILE elements a digit histogram, per chunk of SC_CHUNK tiles the
+// in-chunk exclusive prefixes and chunk totals, the chunk bases over all chunks, then the scatter
+// of every tile to digit_base[d] + its chunk's base + its in-chunk prefix. Same arguments and
+// result as a chained-scan partition, without its look-back state; tile_hist and chunk are scratch.
+constexpr int SC_THREADS = 512;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;  // 4096
+constexpr int SC_CHUNK = 16;                    // tiles per chunk (in-chunk prefix < 2^16)
+struct PartitionArgs {
     uint64_t N;
     const uint32_t *gs_in;  uint32_t *gs_out;   // null when sorting by key bits
     const void *key_in;     void *key_out;
@@ -92,14 +98,14 @@ struct OnesweepArgs {
     const uint32_t *row_in; uint32_t *row_out;  // nullable
     int key_digits;         // 1: digit from the key's order image, 0: from gs
     int shift, bits;
-    const uint32_t *digit_base;       // [RADIX_BINS] exclusive global offsets of this pass
-    unsigned long long *lookback;     // [tiles * RADIX_BINS]
-    uint32_t *ticket;
-    uint32_t epoch;
-    uint32_t *err;
+    const uint32_t *digit_base;  // [RADIX_BINS] exclusive global offsets of this pass
+    uint16_t *tile_hist;    // [tiles * RADIX_BINS] scratch
+    uint32_t *chunk;        // [chunks * RADIX_BINS] scratch
     int key_bytes, dtype;
 };
-cudaError_t launch_onesweep(const OnesweepArgs &a, cudaStream_t s);
+inline uint64_t partition_tiles(uint64_t N) { return (N + SC_TILE - 1) / SC_TILE; }
+inline uint64_t partition_chunks(uint64_t N) { return (partition_tiles(N) + SC_CHUNK - 1) / SC_CHUNK; }
+cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t s);
 // exclusive scans of the per-pass histograms -> digit bases
 cudaError_t launch_digit_bases(const uint32_t *hist, uint32_t *bases, int npass, cudaStream_t s);
 // histogram of key digits for a key sort

@@ -3,14 +3,15 @@
 //   * by the bucket index of each element's predicted position, so that every on-chip bucket of
 //     positions ends up contiguous and in input order (which keeps the paper's first-arrival rule
 //     and the conflict arrays' arrival order intact inside a bucket), and
-//   * by the key's order image, as the radix sort behind the training sample (Sec. "Training").
+//   * by the key's order image, as the radix sort behind the training sample (Sec. "Training"),
+//     the multi-block sorts of oversized buckets and long repairs, and the "no model" reference.
 //
-// One pass reads and writes each element once. A tile ranks its elements per digit stably (a warp
-// finds the lanes holding the same digit from one ballot per digit bit, then counts them with popc),
-// publishes its per-digit counts, and learns its global offsets by decoupled look-back over earlier
-// tiles, eight at a time (tiles are numbered by an atomic ticket, so every tile waited on has already
-// started). Writes go out through a shared-memory reorder buffer in digit order, so each digit's
-// run leaves as coalesced stores.
+// One pass reads and writes each element once, in tiles of 4,096. Its offsets come from a scan
+// over per-tile digit histograms (reduce, then scan, then scatter), so no block ever waits on
+// another and two blocks share each SM. A tile ranks its elements per digit stably (a warp finds the
+// lanes holding the same digit from one ballot per digit bit, then counts them with popc); writes
+// go out through a shared-memory reorder buffer in digit order, so each digit's run leaves as
+// coalesced stores.
 #include <algorithm>
 #include <type_traits>
 
@@ -26,53 +27,135 @@ static inline cudaError_t nns_launched(cudaError_t e, int k = 1) {
 
 namespace nns {
 
+// ---------------------------------------------------------------------------------------------
+// The partition pass without look-back. The tiles' global offsets come from a scan over tile
+// histograms instead of from waits on earlier tiles, so every block is independent: two blocks run
+// on each SM and one block's loads overlap the other's ranking and stores.
 namespace {
-constexpr int NW = PART_THREADS / 32;
-constexpr unsigned long long FLAG_AGG = 1ull, FLAG_INCL = 2ull;
-constexpr unsigned long long VAL_MASK = (1ull << 46) - 1ull;
+constexpr int SC_NW = SC_THREADS / 32;
 
-__device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, unsigned long long flag,
-                                                      unsigned long long v) {
-    return ((unsigned long long)(epoch & 0xFFFFu) << 48) | (flag << 46) | (v & VAL_MASK);
+template <typename W, bool KEYDIG>
+__device__ __forceinline__ uint32_t sc_digit(const PartitionArgs &a, W key, uint32_t gs, uint32_t mask) {
+    if constexpr (KEYDIG) return (uint32_t)(ordbits(word64(key), a.dtype) >> a.shift) & mask;
+    else return (gs >> a.shift) & mask;
+}
+}  // namespace
+
+// per tile: the digit histogram (per-warp counters, so that equal digits contend within a warp only)
+template <typename W, bool KEYDIG>
+__global__ void __launch_bounds__(SC_THREADS) k_tile_hist(PartitionArgs a) {
+    __shared__ uint32_t h[SC_NW][RADIX_BINS];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = lane; i < RADIX_BINS; i += 32) h[w][i] = 0;
+    __syncwarp();
+    const uint64_t base = (uint64_t)blockIdx.x * SC_TILE;
+    const uint32_t cnt = (uint32_t)min((uint64_t)SC_TILE, a.N - base);
+    const uint32_t mask = (1u << a.bits) - 1u;
+    const W *kin = reinterpret_cast<const W *>(a.key_in);
+    uint32_t d[SC_ITEMS];
+#pragma unroll
+    for (int r = 0; r < SC_ITEMS; ++r) {
+        const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
+        d[r] = 0xFFFFFFFFu;
+        if (loc < cnt) {
+            if constexpr (KEYDIG) d[r] = sc_digit<W, true>(a, kin[base + loc], 0u, mask);
+            else d[r] = sc_digit<W, false>(a, W(0), a.gs_in[base + loc], mask);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < SC_ITEMS; ++r)
+        if (d[r] != 0xFFFFFFFFu) atomicAdd(&h[w][d[r]], 1u);
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int ww = 0; ww < SC_NW; ++ww) t += h[ww][tid];  // SC_THREADS == RADIX_BINS
+    a.tile_hist[(size_t)blockIdx.x * RADIX_BINS + tid] = (uint16_t)t;
 }
 
-struct PartSmem {
-    uint16_t cnt[NW][RADIX_BINS];
-    uint16_t dsort[PART_TILE];
-    alignas(16) unsigned char buf[PART_TILE * 8];
+// per chunk of SC_CHUNK tiles: each tile's histogram becomes its exclusive prefix inside the chunk,
+// and the chunk's totals go to chunk[c]
+__global__ void __launch_bounds__(RADIX_BINS) k_chunk_prefix(PartitionArgs a, uint32_t tiles) {
+    const uint32_t c = blockIdx.x, d = threadIdx.x;
+    const uint32_t t0 = c * SC_CHUNK;
+    uint16_t v[SC_CHUNK];
+#pragma unroll
+    for (int j = 0; j < SC_CHUNK; ++j)
+        v[j] = (t0 + j < tiles) ? a.tile_hist[(size_t)(t0 + j) * RADIX_BINS + d] : (uint16_t)0;
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < SC_CHUNK; ++j) {
+        if (t0 + j < tiles) a.tile_hist[(size_t)(t0 + j) * RADIX_BINS + d] = (uint16_t)run;
+        run += v[j];
+    }
+    a.chunk[(size_t)c * RADIX_BINS + d] = run;
+}
+
+// chunk totals -> chunk bases, digit_base[d] + the sum over earlier chunks, in place. Block b takes
+// digits [32 b, 32 b + 32); its 32 warps take consecutive groups of chunks (lane = digit, so every
+// load and store of a warp is one 128-byte line)
+__global__ void __launch_bounds__(1024) k_chunk_base(PartitionArgs a, uint32_t chunks) {
+    __shared__ uint32_t part[32][33];
+    const int i = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const uint32_t d = blockIdx.x * 32 + i;
+    const uint32_t G = (chunks + 31) / 32;
+    const uint32_t c0 = min(chunks, (uint32_t)j * G), c1 = min(chunks, c0 + G);
+    uint32_t sum = 0;
+    for (uint32_t c = c0; c < c1; ++c) sum += a.chunk[(size_t)c * RADIX_BINS + d];
+    part[j][i] = sum;
+    __syncthreads();
+    if (j == 0) {
+        uint32_t run = a.digit_base[d];
+        for (int q = 0; q < 32; ++q) {
+            const uint32_t x = part[q][i];
+            part[q][i] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    uint32_t run = part[j][i];
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t x = a.chunk[(size_t)c * RADIX_BINS + d];
+        a.chunk[(size_t)c * RADIX_BINS + d] = run;
+        run += x;
+    }
+}
+
+namespace {
+struct ScSmem {
+    uint16_t cnt[SC_NW][RADIX_BINS];
+    uint16_t dsort[SC_TILE];
+    alignas(16) unsigned char buf[SC_TILE * 8];
 };
 }  // namespace
 
-template <typename W, bool KEYDIG, bool PAY, bool ROW>
-__global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
+// per tile: stable rank of every element by digit, then the scatter to its global position through
+// a shared-memory reorder buffer (each digit's run leaves as coalesced stores)
+template <typename W, bool KEYDIG, bool PAY, bool ROW, int MINB>
+__global__ void __launch_bounds__(SC_THREADS, MINB) k_scatter(PartitionArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    PartSmem &S = *reinterpret_cast<PartSmem *>(smraw);
+    ScSmem &S = *reinterpret_cast<ScSmem *>(smraw);
     __shared__ uint32_t lstart[RADIX_BINS];
     __shared__ uint32_t gofs[RADIX_BINS];
     __shared__ uint32_t scratch[33];
-    __shared__ uint32_t sh_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t nbins = 1u << a.bits;
-    const uint32_t mask = nbins - 1u;
-    if (tid == 0) sh_tile = atomicAdd(a.ticket, 1u);
+    const uint32_t mask = (1u << a.bits) - 1u;
     for (int i = lane; i < RADIX_BINS; i += 32) S.cnt[w][i] = 0;
-    __syncthreads();
-    const uint32_t tile = sh_tile;
-    const uint64_t base = (uint64_t)tile * PART_TILE;
-    if (base >= a.N) return;  // more blocks than tiles (never launched that way)
-    const uint32_t cnt_tile = (uint32_t)std::min<uint64_t>(PART_TILE, a.N - base);
+    const uint32_t tile = blockIdx.x;
+    const uint64_t base = (uint64_t)tile * SC_TILE;
+    const uint32_t cnt_tile = (uint32_t)min((uint64_t)SC_TILE, a.N - base);
+    // this tile's global digit offsets: chunk base + in-chunk prefix (read early, used late)
+    const uint32_t off_in = (uint32_t)a.chunk[(size_t)(tile / SC_CHUNK) * RADIX_BINS + tid] +
+                            (uint32_t)a.tile_hist[(size_t)tile * RADIX_BINS + tid];
 
-    uint32_t gsv[PART_ITEMS], pay[PART_ITEMS], row[PART_ITEMS];
-    W key[PART_ITEMS];
-    uint16_t dig[PART_ITEMS];
-    uint16_t wr[PART_ITEMS];
+    uint32_t gsv[SC_ITEMS], pay[SC_ITEMS], row[SC_ITEMS];
+    W key[SC_ITEMS];
+    uint16_t dig[SC_ITEMS], wr[SC_ITEMS];
     const W *kin = reinterpret_cast<const W *>(a.key_in);
     const unsigned lt = (1u << lane) - 1u;
-    // all of the tile's loads first, so they are in flight together
 #pragma unroll
-    for (int r = 0; r < PART_ITEMS; ++r) {
-        const uint32_t loc = (uint32_t)w * (32 * PART_ITEMS) + r * 32 + lane;
+    for (int r = 0; r < SC_ITEMS; ++r) {
+        const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
         const uint64_t e = base + loc;
         if (loc < cnt_tile) {
             key[r] = kin[e];
@@ -81,22 +164,18 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
             if constexpr (ROW) row[r] = a.row_in[e];
         }
     }
+    __syncwarp();
 #pragma unroll
-    for (int r = 0; r < PART_ITEMS; ++r) {
-        const uint32_t loc = (uint32_t)w * (32 * PART_ITEMS) + r * 32 + lane;
+    for (int r = 0; r < SC_ITEMS; ++r) {
+        const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
         const bool valid = loc < cnt_tile;
         uint32_t d = 0xFFFFu;
-        if (valid) {
-            if constexpr (KEYDIG)
-                d = (uint32_t)(ordbits(word64(key[r]), a.dtype) >> a.shift) & mask;
-            else
-                d = (gsv[r] >> a.shift) & mask;
-        }
+        if (valid) d = sc_digit<W, KEYDIG>(a, key[r], KEYDIG ? 0u : gsv[r], mask);
         dig[r] = (uint16_t)d;
-        // lanes with the same digit: one ballot per digit bit (cheaper than a match on this part;
-        // in a partial tile the invalid lanes are told apart by one more ballot)
+        // lanes holding the same digit: one ballot per digit bit (the invalid lanes of a partial
+        // tile are told apart by one more ballot)
         unsigned peers = 0xFFFFFFFFu;
-        if (cnt_tile != PART_TILE) {
+        if (cnt_tile != SC_TILE) {
             peers = __ballot_sync(0xFFFFFFFFu, valid);
             if (!valid) peers = ~peers;
         }
@@ -115,11 +194,10 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
         __syncwarp();
     }
     __syncthreads();
-    // per-digit tile totals and warp-exclusive prefixes
     uint32_t total = 0;
     {
-        const int d = tid;  // PART_THREADS == RADIX_BINS
-        for (int ww = 0; ww < NW; ++ww) {
+        const int d = tid;  // SC_THREADS == RADIX_BINS
+        for (int ww = 0; ww < SC_NW; ++ww) {
             const uint32_t c = S.cnt[ww][d];
             S.cnt[ww][d] = (uint16_t)total;
             total += c;
@@ -127,76 +205,28 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
     }
     const uint32_t ls = block_excl_sum(total, scratch, nullptr);
     lstart[tid] = ls;
-    // decoupled look-back for digit tid
-    if ((uint32_t)tid < nbins) {
-        unsigned long long *lb = a.lookback + (size_t)tile * RADIX_BINS + tid;
-        unsigned long long excl = 0;
-        if (tile == 0) {
-            st_release_u64(lb, lb_pack(a.epoch, FLAG_INCL, total));
-        } else {
-            st_release_u64(lb, lb_pack(a.epoch, FLAG_AGG, total));
-            // eight predecessors per round trip: their words are read together (each word carries
-            // its own flag and value, so no ordering between them is needed), then taken in order
-            // until an inclusive prefix ends the walk or a tile that has not published stops it
-            constexpr int LBW = 8;
-            long long p = (long long)tile - 1;
-            unsigned long long t0 = 0;
-            uint32_t polls = 0;
-            bool done = false;
-            while (!done) {
-                unsigned long long v[LBW];
-#pragma unroll
-                for (int q = 0; q < LBW; ++q)
-                    v[q] = (p - q >= 0) ? ld_relaxed_u64(a.lookback + (size_t)(p - q) * RADIX_BINS + tid)
-                                        : 0ull;
-                int used = 0;
-#pragma unroll
-                for (int q = 0; q < LBW; ++q) {
-                    if (used != q || p - q < 0) break;
-                    const unsigned long long flag = (v[q] >> 46) & 3ull;
-                    if ((uint32_t)(v[q] >> 48) != (a.epoch & 0xFFFFu) || flag == 0) break;
-                    excl += v[q] & VAL_MASK;
-                    used = q + 1;
-                    if (flag == FLAG_INCL) { done = true; break; }
-                }
-                p -= used;
-                if (done || p < 0) break;  // tile 0 publishes an inclusive prefix: p < 0 is not reached
-                if (used) continue;
-                const unsigned long long now = globaltimer_ns();
-                if (t0 == 0) t0 = now;
-                else if (now - t0 > SPIN_LIMIT_NS || ++polls > SPIN_LIMIT_POLLS) {
-                    atomicOr(a.err, ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
-            }
-            st_release_u64(lb, lb_pack(a.epoch, FLAG_INCL, excl + total));
-        }
-        gofs[tid] = a.digit_base[tid] + (uint32_t)excl - ls;
-    }
+    gofs[tid] = off_in - ls;
     __syncthreads();
-    // local positions
-    uint16_t lpos[PART_ITEMS];
+    uint16_t lpos[SC_ITEMS];
 #pragma unroll
-    for (int r = 0; r < PART_ITEMS; ++r) {
-        const uint32_t loc = (uint32_t)w * (32 * PART_ITEMS) + r * 32 + lane;
+    for (int r = 0; r < SC_ITEMS; ++r) {
+        const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
         if (loc < cnt_tile) {
             const uint32_t d = dig[r];
             lpos[r] = (uint16_t)(lstart[d] + S.cnt[w][d] + wr[r]);
             S.dsort[lpos[r]] = (uint16_t)d;
         }
     }
-    // move each array through the reorder buffer
     auto emit = [&](auto *vals, auto *out) {
         using T = typename std::remove_pointer<decltype(out)>::type;
         T *b = reinterpret_cast<T *>(S.buf);
 #pragma unroll
-        for (int r = 0; r < PART_ITEMS; ++r) {
-            const uint32_t loc = (uint32_t)w * (32 * PART_ITEMS) + r * 32 + lane;
+        for (int r = 0; r < SC_ITEMS; ++r) {
+            const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
             if (loc < cnt_tile) b[lpos[r]] = (T)vals[r];
         }
         __syncthreads();
-        for (uint32_t i = tid; i < cnt_tile; i += PART_THREADS) {
+        for (uint32_t i = tid; i < cnt_tile; i += SC_THREADS) {
             const uint32_t d = S.dsort[i];
             out[(size_t)(uint32_t)(gofs[d] + i)] = b[i];
         }
@@ -210,31 +240,39 @@ __global__ void __launch_bounds__(PART_THREADS, 1) k_onesweep(OnesweepArgs a) {
 }
 
 template <typename W, bool KD>
-static cudaError_t os_go2(const OnesweepArgs &a, cudaStream_t s) {
-    const uint64_t tiles = (a.N + PART_TILE - 1) / PART_TILE;
-    const size_t smem = sizeof(PartSmem);
+static cudaError_t sc_go(const PartitionArgs &a, cudaStream_t s) {
+    const uint64_t tiles = partition_tiles(a.N), chunks = partition_chunks(a.N);
+    k_tile_hist<W, KD><<<(unsigned)tiles, SC_THREADS, 0, s>>>(a);
+    cudaError_t e = nns_launched(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+    k_chunk_prefix<<<(unsigned)chunks, RADIX_BINS, 0, s>>>(a, (uint32_t)tiles);
+    if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    k_chunk_base<<<RADIX_BINS / 32, 1024, 0, s>>>(a, (uint32_t)chunks);
+    if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+    const size_t smem = sizeof(ScSmem);
     const bool pay = a.pay_in != nullptr, row = a.row_in != nullptr;
-#define NNS_OS(P, R)                                                                              \
+#define NNS_SC(P, R, MB)                                                                          \
     {                                                                                             \
-        auto kfn = k_onesweep<W, KD, P, R>;                                                       \
-        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                             (int)smem);                                          \
+        auto kfn = k_scatter<W, KD, P, R, MB>;                                                    \
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
         if (e != cudaSuccess) return e;                                                           \
-        kfn<<<(unsigned)tiles, PART_THREADS, smem, s>>>(a);                                       \
-        return nns_launched(cudaGetLastError());                                                                \
+        kfn<<<(unsigned)tiles, SC_THREADS, smem, s>>>(a);                                         \
+        return nns_launched(cudaGetLastError());                                                  \
     }
-    if (pay && row) NNS_OS(true, true)
-    if (pay) NNS_OS(true, false)
-    if (row) NNS_OS(false, true)
-    NNS_OS(false, false)
-#undef NNS_OS
+    // two resident blocks per SM where the element's registers allow it (4-byte keys)
+    constexpr int MB = sizeof(W) == 4 ? 2 : 1;
+    if (pay && row) NNS_SC(true, true, 1)
+    if (pay) NNS_SC(true, false, MB)
+    if (row) NNS_SC(false, true, MB)
+    NNS_SC(false, false, MB)
+#undef NNS_SC
 }
 
-cudaError_t launch_onesweep(const OnesweepArgs &a, cudaStream_t s) {
+cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t s) {
     if (a.N == 0) return cudaSuccess;
     if (a.key_bytes == 4)
-        return a.key_digits ? os_go2<uint32_t, true>(a, s) : os_go2<uint32_t, false>(a, s);
-    return a.key_digits ? os_go2<uint64_t, true>(a, s) : os_go2<uint64_t, false>(a, s);
+        return a.key_digits ? sc_go<uint32_t, true>(a, s) : sc_go<uint32_t, false>(a, s);
+    return a.key_digits ? sc_go<uint64_t, true>(a, s) : sc_go<uint64_t, false>(a, s);
 }
 
 // exclusive scan of each pass's histogram (one block per pass)

@@ -24,11 +24,13 @@ namespace {
 
 constexpr uint64_t NA_MAX_N = NNSORT_NOALLOC_MAX_N;
 constexpr uint32_t NA_MAX_BUCKETS = 1024;
-constexpr uint64_t NA_MAX_TILES = (NA_MAX_N + PART_TILE - 1) / PART_TILE;
+constexpr uint64_t NA_MAX_TILES = (NA_MAX_N + SC_TILE - 1) / SC_TILE;
+constexpr uint64_t NA_MAX_CHUNKS = (NA_MAX_TILES + SC_CHUNK - 1) / SC_CHUNK;
 constexpr size_t NA_PER_ELEM = 2 * 4 + 2 * 8 + 2 * 4 + 1 + 1 + 2 * 4;  // gs, keys, payload, rank,
                                                                       // flag, two index lists
 constexpr size_t NA_BYTES = NA_MAX_N * NA_PER_ELEM + (size_t)NA_MAX_BUCKETS * (4 + 2 * MAXR * 16 + 32) +
-                            NA_MAX_TILES * RADIX_BINS * 8 + 2 * MAX_PASSES * RADIX_BINS * 4 +
+                            NA_MAX_TILES * RADIX_BINS * 2 + NA_MAX_CHUNKS * RADIX_BINS * 4 +
+                            2 * MAX_PASSES * RADIX_BINS * 4 +
                             (size_t)(NA_MAX_BUCKETS + 1) * sizeof(SeamRange) + 64 * 1024;
 
 // the scratch: one per device that loads the library, held until the process exits
@@ -36,7 +38,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 struct DevState {
     unsigned char *base = nullptr;  // device address of g_noalloc_scratch on this device
-    uint32_t epoch = 0;             // look-back epoch of the last partition pass
 };
 std::mutex g_na_mu;
 DevState g_na_dev[64];
@@ -54,12 +55,12 @@ thread_local int g_na_cuda = 0;
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct NaLayout {
-    Seg *seg; SegStats *stats; uint32_t *err, *hist, *bases, *tickets;
+    Seg *seg; SegStats *stats; uint32_t *err, *hist, *bases;
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2];
     uint8_t *rank, *flag; uint32_t *gx, *gy, *bstart;
     OKey *bmax, *carry, *blo, *bhi;
     SeamRange *ranges; uint32_t *seam_cnt;
-    unsigned long long *lookback;
+    uint16_t *tile_hist; uint32_t *chunk;
     size_t end;
 };
 
@@ -72,7 +73,6 @@ NaLayout na_carve(unsigned char *b) {
     L.err = reinterpret_cast<uint32_t *>(take(16));
     L.hist = reinterpret_cast<uint32_t *>(take(4 * MAX_PASSES * RADIX_BINS));
     L.bases = reinterpret_cast<uint32_t *>(take(4 * MAX_PASSES * RADIX_BINS));
-    L.tickets = reinterpret_cast<uint32_t *>(take(4 * MAX_PASSES * 4));
     for (int i = 0; i < 2; ++i) {
         L.gs[i] = reinterpret_cast<uint32_t *>(take(4 * NA_MAX_N));
         L.key[i] = take(8 * NA_MAX_N);
@@ -89,13 +89,14 @@ NaLayout na_carve(unsigned char *b) {
     L.bhi = reinterpret_cast<OKey *>(take(sizeof(OKey) * NA_MAX_BUCKETS));
     L.ranges = reinterpret_cast<SeamRange *>(take(sizeof(SeamRange) * (NA_MAX_BUCKETS + 1)));
     L.seam_cnt = reinterpret_cast<uint32_t *>(take(16));
-    L.lookback = reinterpret_cast<unsigned long long *>(take(8 * NA_MAX_TILES * RADIX_BINS));
+    L.tile_hist = reinterpret_cast<uint16_t *>(take(2 * NA_MAX_TILES * RADIX_BINS));
+    L.chunk = reinterpret_cast<uint32_t *>(take(4 * NA_MAX_CHUNKS * RADIX_BINS));
     L.end = o;
     return L;
 }
 
-// one-time set-up on the current device: the scratch's device address, a zeroed look-back area
-int na_setup(int dev, cudaStream_t s, DevState **out) {
+// one-time set-up on the current device: the scratch's device address
+int na_setup(int dev, DevState **out) {
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (dev < 0 || dev >= 64) return NNSORT_E_INVALID_ARG;
     DevState &d = g_na_dev[dev];
@@ -103,10 +104,7 @@ int na_setup(int dev, cudaStream_t s, DevState **out) {
         unsigned char *p = nullptr;
         NA_CK(cudaGetSymbolAddress((void **)&p, g_noalloc_scratch));
         if (na_carve(p).end > NA_BYTES) return NNSORT_E_INVALID_ARG;  // layout/size mismatch
-        NaLayout L = na_carve(p);
-        NA_CK(cudaMemsetAsync(L.lookback, 0, 8 * NA_MAX_TILES * RADIX_BINS, s));
         d.base = p;
-        d.epoch = 0;
     }
     *out = &d;
     return NNSORT_OK;
@@ -173,7 +171,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     int dev = 0;
     NA_CK(cudaGetDevice(&dev));
     DevState *ds = nullptr;
-    int rc = na_setup(dev, s, &ds);
+    int rc = na_setup(dev, &ds);
     if (rc) return rc;
     NaLayout L = na_carve(ds->base);
     const int kb = na_kb(dtype);
@@ -183,7 +181,6 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     NA_CK(cudaMemsetAsync(L.stats, 0, sizeof(SegStats), s));
     NA_CK(cudaMemsetAsync(L.err, 0, 16, s));
     NA_CK(cudaMemsetAsync(L.hist, 0, 4 * MAX_PASSES * RADIX_BINS, s));
-    NA_CK(cudaMemsetAsync(L.tickets, 0, 4 * MAX_PASSES * 4, s));
 
     PredictArgs pa{};
     pa.segs = L.seg;
@@ -206,11 +203,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     NA_CK(launch_digit_bases(L.hist, L.bases, pp.npass, s));
     for (int p = 0; p < pp.npass; ++p) {
         const int si = p & 1, di = si ^ 1;
-        if (++ds->epoch >= 0xFFFFu) {
-            NA_CK(cudaMemsetAsync(L.lookback, 0, 8 * NA_MAX_TILES * RADIX_BINS, s));
-            ds->epoch = 1;
-        }
-        OnesweepArgs a{};
+        PartitionArgs a{};
         a.N = n;
         a.gs_in = L.gs[si];
         a.gs_out = L.gs[di];
@@ -223,13 +216,11 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
         a.shift = pp.shift[p];
         a.bits = pp.bits[p];
         a.digit_base = L.bases + p * RADIX_BINS;
-        a.lookback = L.lookback;
-        a.ticket = L.tickets + p * 4;
-        a.epoch = ds->epoch;
-        a.err = L.err;
+        a.tile_hist = L.tile_hist;
+        a.chunk = L.chunk;
         a.key_bytes = kb;
         a.dtype = dtype;
-        NA_CK(launch_onesweep(a, s));
+        NA_CK(launch_partition(a, s));
     }
     const int fi = pp.npass & 1, oi = fi ^ 1;
     NA_CK(launch_bucket_bounds(L.gs[fi], n, sg.nb, wlog, L.bstart, s));

@@ -112,8 +112,8 @@ def test_noalloc_tensor_core_form_matches_nnsort_sort():
 def test_noalloc_one_bucket_two_passes_and_repeated_calls():
     """(1) Nearly all keys equal, so one bucket holds ~99% of the 262,144 keys (the one-block
     rounds and sort over global lists); (2) 512-position buckets with m = 1.9, so 973 buckets need
-    two partition passes; run four times in a row so the look-back epochs carry over between
-    calls. Each result equals the oracle's stable sort and nnsort_sort's statistics."""
+    two partition passes; run four times in a row, each call on the scratch the previous one
+    left. Each result equals the oracle's stable sort and nnsort_sort's statistics."""
     n = 262_144
     rs = np.random.RandomState(41)
     dup = np.full(n, 3.5, np.float32)
