@@ -9,10 +9,13 @@
 //   layer 2 (H -> H)  tcgen05.mma.kind::f16, M = 128, N = H, K = H in steps of 16, issued by one
 //                     thread; B = W2 (H x H, K-major) staged once per block; D in TMEM (the split
 //                     form accumulates A_hi W2^T + A_lo W2^T into the same D);
-//   epilogue          tcgen05.ld (thread t reads TMEM lane t = its key's row), + b2, ReLU, output
-//                     layer in binary32 FFMA, position rounding as in the binary32 path.
-// The MMA completion is signalled through an mbarrier whose wait gives up after a time limit
-// (the kernel then raises ERR_TIMEOUT, still frees its tensor memory and returns).
+//                     b2 enters the same accumulator as one more K-step (a constant slab of ones
+//                     times b2 split exactly into three BF16 parts);
+//   epilogue          tcgen05.ld (thread t reads TMEM lane t = its key's row), ReLU, output layer
+//                     in binary32 FFMA, position rounding as in the binary32 path.
+// The MMA completion is signalled through an mbarrier that the issuing thread waits on (the
+// others wait in a barrier behind it); the wait gives up after a time limit (the kernel then raises
+// ERR_TIMEOUT, still frees its tensor memory and returns).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -150,6 +153,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// The second layer's bias enters the MMA as one more K-step of 16: a constant A slab whose first
+// three columns are 1 (every row) and a B slab whose first three columns hold b2 split exactly into
+// three BF16 parts (hi = b2 truncated to 8 significant bits, mid and lo the truncated rests), so
+// D = [1 1 1 0 ..] [b2_hi b2_mid b2_lo 0 ..]^T + A W2^T with b2 carried to binary32 precision.
+// Both slabs use the canonical K-major layout of a 16-wide K block (two 8x8 core matrices along K,
+// LBO = 128 bytes; 8-row groups SBO = 256 bytes apart).
+constexpr uint32_t SLAB_LBO = 128, SLAB_SBO = 256;
+__device__ __forceinline__ uint32_t slab_off(int row, int k) {
+    return (uint32_t)(row / 8) * SLAB_SBO + (uint32_t)(k / 8) * SLAB_LBO + (uint32_t)(row % 8) * 16 +
+           (uint32_t)(k % 8) * 2;
+}
+__device__ __forceinline__ float bf16_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFF0000u); }
+// ones: TC_M x 16; bias: H x 16 (row = output unit)
+template <int H>
+__device__ __forceinline__ void fill_bias_slabs(unsigned char *ones, unsigned char *bias, const float *b2,
+                                                int tid, int nthreads) {
+    for (int e = tid; e < TC_M * 16; e += nthreads) {
+        const int r = e / 16, k = e % 16;
+        *reinterpret_cast<__nv_bfloat16 *>(ones + slab_off(r, k)) = __float2bfloat16_rn(k < 3 ? 1.0f : 0.0f);
+    }
+    for (int e = tid; e < H * 16; e += nthreads) {
+        const int r = e / 16, k = e % 16;
+        const float v = b2[r];
+        const float hi = bf16_trunc(v), mid = bf16_trunc(v - hi), lo = (v - hi) - mid;
+        const float piece = k == 0 ? hi : (k == 1 ? mid : (k == 2 ? lo : 0.0f));
+        *reinterpret_cast<__nv_bfloat16 *>(bias + slab_off(r, k)) = __float2bfloat16_rn(piece);
+    }
+}
+
 __device__ __forceinline__ int seg_of_tile_tc(const Seg *segs, int nseg, uint32_t tile) {
     int lo = 0, hi = nseg - 1;
     while (lo < hi) {
@@ -171,7 +203,8 @@ __host__ __device__ constexpr int tc_ncol(int H, int KPT) {
 template <int H, bool SPLIT, int KPT>
 __host__ __device__ constexpr size_t tc_smem_bytes(int npass) {
     return (size_t)KPT * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)(SPLIT ? 2 : 1) * H * H * 2 +
-           (size_t)(4 * H + 4) * 4 + (size_t)npass * RADIX_BINS * 4;
+           (size_t)TC_M * 16 * 2 + (size_t)H * 16 * 2 + (size_t)(4 * H + 4) * 4 +
+           (size_t)npass * RADIX_BINS * 4;
 }
 
 template <int H, typename W, bool SPLIT, int KPT>
@@ -187,7 +220,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sB = sm + KPT * NT * TILE_B;                       // H x H bf16
     unsigned char *sB16 = sB + H * H * 2;                             // H x H fp16 (split form)
-    float *pf = reinterpret_cast<float *>(sB + (SPLIT ? 2 : 1) * H * H * 2);  // W1 | b1 | b2 | W3 | b3
+    unsigned char *sOnes = sB + (SPLIT ? 2 : 1) * H * H * 2;          // TC_M x 16 bf16
+    unsigned char *sBias = sOnes + TC_M * 16 * 2;                     // H x 16 bf16
+    float *pf = reinterpret_cast<float *>(sBias + H * 16 * 2);      // W1 | b1 | b2 | W3 | b3
     const float4 *pv = reinterpret_cast<const float4 *>(pf);
     uint32_t *sh_hist = reinterpret_cast<uint32_t *>(pf + 4 * H + 4);
     __shared__ __align__(8) unsigned long long bar;
@@ -248,6 +283,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                 pf[3 * H + e] = sg.params[3 * H + H * H + e];  // W3
             }
             if (tid == 0) pf[4 * H] = sg.params[4 * H + H * H];  // b3
+            fill_bias_slabs<H>(sOnes, sBias, sg.params + 2 * H + H * H, tid, TC_THREADS);
             loaded = si;
             fence_async_smem();
             __syncthreads();
@@ -331,10 +367,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
 #pragma unroll
                 for (int g = 0; g < KPT; ++g) {
                     const uint32_t a0 = smem_u32(sm + (g * NT) * TILE_B);
+                    // the bias slab first (it starts the accumulator), then A_hi W2^T (and A_lo W2^T)
+                    mma_bf16(tbase + g * H, mdesc(smem_u32(sOnes), SLAB_LBO, SLAB_SBO),
+                             mdesc(smem_u32(sBias), SLAB_LBO, SLAB_SBO), idesc, 0u);
 #pragma unroll
                     for (int ks = 0; ks < H / 16; ++ks)
                         mma_bf16(tbase + g * H, mdesc(a0 + ks * 2 * LBO, LBO, SBO),
-                                 mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc, ks > 0 ? 1u : 0u);
+                                 mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc, 1u);
                     if (SPLIT) {
 #pragma unroll
                         for (int ks = 0; ks < H / 16; ++ks)
@@ -343,11 +382,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                     }
                 }
                 mma_commit(smem_u32(&bar));
-            }
-            if (!dead && !mbar_wait(smem_u32(&bar), phase)) {
-                dead = true;
-                dead_parity = phase;
-                err |= ERR_TIMEOUT;
+                // one thread waits for the MMAs; the others sleep in the barrier below
+                if (!mbar_wait(smem_u32(&bar), phase)) {
+                    dead = true;
+                    dead_parity = phase;
+                    err |= ERR_TIMEOUT;
+                }
+                tc_fence_before();
             }
             phase ^= 1u;
             dead = __syncthreads_or(dead);
@@ -358,11 +399,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
             for (int g = 0; g < KPT; ++g) yy[g] = pk2(pf[4 * H], 0.0f);
 #pragma unroll
             for (int c0 = 0; c0 < H; c0 += 16) {
-                float b2[16], w3[16];
+                float w3[16];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    const float4 bq = pv[2 * H / 4 + c0 / 4 + v], wq = pv[3 * H / 4 + c0 / 4 + v];
-                    b2[4 * v] = bq.x; b2[4 * v + 1] = bq.y; b2[4 * v + 2] = bq.z; b2[4 * v + 3] = bq.w;
+                    const float4 wq = pv[3 * H / 4 + c0 / 4 + v];
                     w3[4 * v] = wq.x; w3[4 * v + 1] = wq.y; w3[4 * v + 2] = wq.z; w3[4 * v + 3] = wq.w;
                 }
 #pragma unroll
@@ -376,11 +416,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
                         for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
                     }
 #pragma unroll
-                    for (int q = 0; q < 16; q += 2) {
-                        float t0, t1;
-                        upk2(add2_rn(pk2(acc[q], acc[q + 1]), pk2(b2[q], b2[q + 1])), t0, t1);
-                        yy[g] = fma2_rn(pk2(w3[q], w3[q + 1]), pk2(relu_f(t0), relu_f(t1)), yy[g]);
-                    }
+                    for (int q = 0; q < 16; q += 2)
+                        yy[g] = fma2_rn(pk2(w3[q], w3[q + 1]), pk2(relu_f(acc[q]), relu_f(acc[q + 1])), yy[g]);
                 }
             }
 #pragma unroll
@@ -460,7 +497,8 @@ __device__ __forceinline__ bool grp_or(int id, bool v) {
 template <int H, bool SPLIT, int NG>
 __host__ __device__ constexpr size_t tcmg_smem_bytes(int npass) {
     return (size_t)NG * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)(SPLIT ? 2 : 1) * H * H * 2 +
-           (size_t)(4 * H + 4) * 4 + (size_t)npass * RADIX_BINS * 4;
+           (size_t)TC_M * 16 * 2 + (size_t)H * 16 * 2 + (size_t)(4 * H + 4) * 4 +
+           (size_t)npass * RADIX_BINS * 4;
 }
 
 template <int H, typename W, bool SPLIT, int NG>
@@ -475,7 +513,9 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *sB = sm + NG * NT * TILE_B;
     unsigned char *sB16 = sB + H * H * 2;
-    float *pf = reinterpret_cast<float *>(sB + NT * H * H * 2);  // W1 | b1 | b2 | W3 | b3
+    unsigned char *sOnes = sB + NT * H * H * 2;                       // TC_M x 16 bf16
+    unsigned char *sBias = sOnes + TC_M * 16 * 2;                     // H x 16 bf16
+    float *pf = reinterpret_cast<float *>(sBias + H * 16 * 2);      // W1 | b1 | b2 | W3 | b3
     const float4 *pv = reinterpret_cast<const float4 *>(pf);
     uint32_t *sh_hist = reinterpret_cast<uint32_t *>(pf + 4 * H + 4);
     __shared__ __align__(8) unsigned long long bar[NG];
@@ -506,6 +546,7 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
             pf[3 * H + e] = sg.params[3 * H + H * H + e];
         }
         if (tid == 0) pf[4 * H] = sg.params[4 * H + H * H];
+        fill_bias_slabs<H>(sOnes, sBias, sg.params + 2 * H + H * H, tid, NG * TC_THREADS);
     }
     fence_async_smem();
     tc_fence_before();
@@ -576,10 +617,12 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
         tc_fence_after();
         if (gt == 0 && !dead) {
             const uint32_t a0 = smem_u32(myA), b0 = smem_u32(sB);
+            // the bias slab first (it starts the accumulator), then A_hi W2^T (and A_lo W2^T)
+            mma_bf16(dcol, mdesc(smem_u32(sOnes), SLAB_LBO, SLAB_SBO), mdesc(smem_u32(sBias), SLAB_LBO, SLAB_SBO),
+                     idesc, 0u);
 #pragma unroll
             for (int ks = 0; ks < H / 16; ++ks)
-                mma_bf16(dcol, mdesc(a0 + ks * 2 * LBO, LBO, SBO), mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc,
-                         ks > 0 ? 1u : 0u);
+                mma_bf16(dcol, mdesc(a0 + ks * 2 * LBO, LBO, SBO), mdesc(b0 + ks * 2 * LBO, LBO, SBO), idesc, 1u);
             if (SPLIT) {
 #pragma unroll
                 for (int ks = 0; ks < H / 16; ++ks)
@@ -587,11 +630,13 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
                              mdesc(smem_u32(sB16) + ks * 2 * LBO, LBO, SBO), idesc_lo, 1u);
             }
             mma_commit(mybar);
-        }
-        if (!dead && !mbar_wait(mybar, phase)) {
-            dead = true;
-            dead_parity = phase;
-            err |= ERR_TIMEOUT;
+            // one thread of the group waits for the MMAs; the others sleep in the barrier below
+            if (!mbar_wait(mybar, phase)) {
+                dead = true;
+                dead_parity = phase;
+                err |= ERR_TIMEOUT;
+            }
+            tc_fence_before();
         }
         phase ^= 1u;
         dead = grp_or(bid, dead);
@@ -609,12 +654,9 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const float4 bq = pv[2 * H / 4 + c0 / 4 + v], wq = pv[3 * H / 4 + c0 / 4 + v];
-                float t0, t1, t2, t3;
-                upk2(add2_rn(pk2(acc[4 * v], acc[4 * v + 1]), pk2(bq.x, bq.y)), t0, t1);
-                upk2(add2_rn(pk2(acc[4 * v + 2], acc[4 * v + 3]), pk2(bq.z, bq.w)), t2, t3);
-                yy = fma2_rn(pk2(wq.x, wq.y), pk2(relu_f(t0), relu_f(t1)), yy);
-                yy = fma2_rn(pk2(wq.z, wq.w), pk2(relu_f(t2), relu_f(t3)), yy);
+                const float4 wq = pv[3 * H / 4 + c0 / 4 + v];
+                yy = fma2_rn(pk2(wq.x, wq.y), pk2(relu_f(acc[4 * v]), relu_f(acc[4 * v + 1])), yy);
+                yy = fma2_rn(pk2(wq.z, wq.w), pk2(relu_f(acc[4 * v + 2]), relu_f(acc[4 * v + 3])), yy);
             }
         }
         tc_fence_before();
