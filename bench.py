@@ -1,18 +1,21 @@
 #!/usr/bin/env python
 """Benchmark: NN-sort on one GB300 (or N independent replicas under torchrun).
 
-Workload (the large single-GPU configuration): 268,435,456 float32 keys, lognormal(0, 2) with 5%
-exact duplicates, shuffled, keys only; model f = MLP 1 -> 64 -> 64 -> 1 trained on the device
-(1% sample, 100 Adam steps, mini-batch 65,536, lr 1e-2); m = 1.25, eps = 3, tau = 1024.
+Headline workload (the large single-GPU configuration): 268,435,456 float32 keys, lognormal(0, 2)
+with 5% exact duplicates, shuffled, keys only; model f = MLP 1 -> 64 -> 64 -> 1 trained on the
+device (1% sample, 100 Adam steps, mini-batch 65,536, lr 1e-2); m = 1.25, tau = 1024.
 
 One step = the whole job on one resident input: sample + labels, training, prediction, partition,
 rounds, polish, merge/repair. Each timed step sorts its own copy of the input (1 GiB, larger than
 L2), so no L2 flush is needed. `value` is keys sorted per second over the whole job; the sort alone,
 the plain binary32 form, the roofline of the dominant kernel, an end-to-end figure through the
-host-array C entry point and the CPU oracle on a bounded sample are reported beside it.
+host-array C entry point and the CPU oracle on a bounded sample are reported beside it, and so are
+the other workloads (1M uniform keys; 64M uint64 keys with payload; a batch of 4,096 arrays against
+one sort call per array; the serving loop), the ablation of the learned map and library CPU sorts.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --experiment shift|quickdraw|eps   (the paper's Exp-3, Exp-2 stand-in, Exp-4)
+  python bench.py --serve-full                        (the serving loop at its full shape alone)
 """
 from __future__ import annotations
 
@@ -38,17 +41,23 @@ WORKLOAD = ("268,435,456 float32 keys lognormal(0,2) with 5% exact duplicates, k
             "MLP 1-64-64-1 trained on the device (1% sample, 100 Adam steps, batch 65536, lr 1e-2); "
             "m=1.25, tau=1024; bucket width, polish blocks per SM and eps from the autotuned table")
 
-# DRAM bytes per key of one launch, from the ncu captures summarised under profiles/ (2^26 keys,
-# same distribution and model recipe; traffic grows in proportion to the keys)
+# DRAM bytes per key of one launch (dram__bytes_read.sum + dram__bytes_write.sum over the keys of
+# the launch) from single-kernel ncu captures at 2^26 keys of the same distribution and model
+# recipe; traffic grows in proportion to the keys. A kernel changed since its capture has no entry.
 TRAFFIC_PER_KEY = {
-    ("predict", "bf16x2"): 7.365,   # profiles/k_predict_bf16_mg_split_64M.md
-    ("rounds", None): 6.805,        # profiles/k_rounds_64M.md
-    ("polish", None): 12.657,       # profiles/k_polish_64M.md
-    ("partition", None): 15.566,    # profiles/k_onesweep_partition_64M.md (per pass)
+    ("predict", "bf16x2"): 7.365,   # k_predict_bf16_mg<64, split>
+    ("rounds", None): 6.805,        # k_rounds
+    ("polish", None): 12.657,       # k_polish
 }
+TRAFFIC_SOURCE = "ncu capture of the kernel at 2^26 keys, scaled to the launch's keys"
 # binary32 operations per key on the CUDA cores in the tensor-core predict (layer 1: H FMA; split
 # form: H residual subtractions; output layer: H additions and H FMA; FMA = 2)
 CUDA_CORE_FLOP_PER_KEY = {"bf16": 2 * 64 + 64 + 2 * 64, "bf16x2": 2 * 64 + 64 + 64 + 2 * 64}
+
+
+def mlp_flop_per_key(layers, h1, h2):
+    """The method's own work per key evaluation: 2 (fan-in x fan-out) summed over the layers."""
+    return 2 * (h1 + h1 * h2 + h2) if layers == 2 else 2 * (h1 + h1)
 
 
 def peaks():
@@ -194,39 +203,62 @@ def reference_arm(args, ws, rank):
 SERVE_TRAIN = dict(layers=2, h1=32, h2=32, sample_n=20_000, steps=100, batch=4096, lr=1e-2)
 
 
-def serving_leg(nns, W, count=200, rate=400.0, seed=5):
-    """Poisson arrivals of float64 requests (log-uniform 10K..4M keys; uniform / lognormal(0,2) /
-    clustered), per-request device-trained 1-32-32-1, 120 GiB admission budget. Continuous
-    batching (2 worker streams, up to 16 requests per batch) against FIFO (1 worker, 1 request
-    per batch). Latency: submit -> sorted result back in host memory."""
-    reqs = W.serving_requests(count=count, seed=seed, lo=10_000, hi=4_000_000, rate_per_s=rate)
-    out = {}
-    for mode, kw in (("continuous_batching", dict(workers=2, max_batch=16)),
-                     ("fifo", dict(workers=1, max_batch=1))):
-        arrays = [r["keys"].copy() for r in reqs]
-        lats = []
-        with nns.Server(hbm_budget=120 << 30, train=SERVE_TRAIN, **kw) as srv:
-            t0 = time.perf_counter()
-            tickets = []
-            for i, r in enumerate(reqs):
-                dt = r["arrival_s"] - (time.perf_counter() - t0)
-                if dt > 0:
-                    time.sleep(dt)
-                tickets.append(srv.submit(arrays[i], seed=i))
-            for t in tickets:
-                _, lat = srv.wait(t)
-                lats.append(lat)
-            wall = time.perf_counter() - t0
-        keys = sum(r["keys"].shape[0] for r in reqs)
-        for i in range(0, count, max(1, count // 8)):
-            assert np.all(arrays[i][1:] >= arrays[i][:-1])
-        out[mode] = {"p50_ms": 1e3 * float(np.percentile(lats, 50)),
-                     "p99_ms": 1e3 * float(np.percentile(lats, 99)),
-                     "mkeys_s": keys / wall / 1e6, "wall_s": wall}
-    out["requests"] = count
-    out["offered_rate_per_s"] = rate
-    out["keys"] = int(sum(r["keys"].shape[0] for r in reqs))
+def _serve_once(nns, reqs, scale, workers, max_batch):
+    """One pass of the request stream through a server: arrivals at reqs' times x `scale` (0 = all
+    at once), each request's array copied fresh. Returns (latencies s, wall s)."""
+    arrays = [r["keys"].copy() for r in reqs]
+    lats = []
+    with nns.Server(hbm_budget=120 << 30, train=SERVE_TRAIN, workers=workers,
+                    max_batch=max_batch) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for i, r in enumerate(reqs):
+            dt = r["arrival_s"] * scale - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(arrays[i], seed=i))
+        for t in tickets:
+            _, lat = srv.wait(t)
+            lats.append(lat)
+        wall = time.perf_counter() - t0
+    for i in range(0, len(reqs), max(1, len(reqs) // 8)):
+        assert np.all(arrays[i][1:] >= arrays[i][:-1])
+    return lats, wall
+
+
+def serving_leg(nns, W, count=300, lo=10_000, hi=16_000_000, repeats=3, seed=5):
+    """float64 requests (log-uniform sizes in [lo, hi]; uniform / lognormal(0,2) / clustered),
+    per-request device-trained 1-32-32-1, 120 GiB admission budget. First a saturation run (every
+    request submitted at once, continuous batching) gives the saturated request rate; then Poisson
+    arrivals at 0.7 x that rate through continuous batching (2 worker streams, up to 16 requests
+    per batch), `repeats` times, and once through FIFO (1 worker, 1 request per batch). Latency:
+    submit -> sorted result back in host memory."""
+    reqs = W.serving_requests(count=count, seed=seed, lo=lo, hi=hi, rate_per_s=1.0)
+    keys = int(sum(r["keys"].shape[0] for r in reqs))
+    _, wall = _serve_once(nns, reqs, 0.0, 2, 16)
+    sat_rate = count / wall
+    rate = 0.7 * sat_rate
+    scale = 1.0 / rate  # arrivals were drawn at 1 request/s
+    out = {"requests": count, "sizes": [lo, hi], "keys": keys,
+           "saturated": {"requests_per_s": sat_rate, "mkeys_s": keys / wall / 1e6},
+           "offered_rate_per_s": rate}
+    runs = []
+    for _ in range(repeats):
+        lats, wall = _serve_once(nns, reqs, scale, 2, 16)
+        runs.append({"p50_ms": 1e3 * float(np.percentile(lats, 50)),
+                     "p99_ms": 1e3 * float(np.percentile(lats, 99)), "mkeys_s": keys / wall / 1e6})
+    out["continuous_batching"] = {
+        "runs": runs, "p50_ms_median": statistics.median(r["p50_ms"] for r in runs),
+        "p99_ms_median": statistics.median(r["p99_ms"] for r in runs),
+        "mkeys_s_median": statistics.median(r["mkeys_s"] for r in runs)}
+    lats, wall = _serve_once(nns, reqs, scale, 1, 1)
+    out["fifo"] = {"p50_ms": 1e3 * float(np.percentile(lats, 50)),
+                   "p99_ms": 1e3 * float(np.percentile(lats, 99)), "mkeys_s": keys / wall / 1e6}
     return out
+
+
+def serving_full(nns, W):
+    return serving_leg(nns, W, count=1000)
 
 
 # --------------------------------------------------------------------------- experiments
@@ -380,6 +412,414 @@ def experiment_eps(nns, W, torch, n, precision):
         del model
 
 
+# --------------------------------------------------------------------------- shared pieces
+STAGES = ["predict", "partition", "bucket_bounds", "rounds", "finalize", "polish", "seam"]
+
+
+def _ev(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def tuned(dtype, n, arch, precision, m=1.25, tau=1024):
+    """m and tau as the paper sets them; bucket width, polish blocks per SM and the round limit eps
+    from the autotuner's table for this workload class."""
+    from paper_1907_08817_gb300 import autotune as AT
+    return dict(m=m, tau=tau, **AT.tuned_options(dtype, n, *arch, precision))
+
+
+def fastest_tensor_form(dtype, n, arch):
+    """The tensor-core form the autotuner measured faster on this workload class."""
+    from paper_1907_08817_gb300 import autotune as AT
+    cands = [(e["sort_ms"], p) for p in ("bf16x2", "bf16")
+             if (e := AT.tuned_entry(dtype, n, *arch, p)) is not None]
+    return min(cands)[1] if cands else "bf16x2"
+
+
+def roofline_of(stage, ms, n, kb, pb, precision, arch, npass, pk):
+    """Roofline entry of one stage of the sort: its algorithmic work for one launch over its mean
+    event time, against the measured peak of the unit that bounds it."""
+    traffic = None
+    tpk = TRAFFIC_PER_KEY.get((stage, precision), TRAFFIC_PER_KEY.get((stage, None)))
+    if tpk is not None and pb == 0 and kb == 4:
+        traffic = tpk * n * (npass if stage == "partition" else 1)
+    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    if stage == "predict" and precision in ("bf16", "bf16x2") and arch[0] == 2:
+        fpk = mlp_flop_per_key(*arch)
+        ach = n * fpk / (ms / 1e3) / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        r = {"kernel": f"predict (k_predict_bf16_mg, {precision})", "bound": "tensor",
+             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "peak_kind": f"bf16 sustained, {pk['source']} (the kernel runs inside a long step)",
+             "frac_of_burst": ach / pk["bf16_tflops"],
+             "work": f"{fpk} FLOP per key (2 x fan-in x fan-out over the layers) x {n} keys",
+             "cuda_cores": {"flop_per_key": CUDA_CORE_FLOP_PER_KEY[precision],
+                            "achieved": n * CUDA_CORE_FLOP_PER_KEY[precision] / (ms / 1e3) / 1e12,
+                            "peak": fp32_peak, "unit": "TFLOP/s",
+                            "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}}
+        r["cuda_cores"]["frac"] = r["cuda_cores"]["achieved"] / fp32_peak
+    elif stage == "predict" and precision == "fp32":
+        fpk = mlp_flop_per_key(*arch)
+        ach = n * fpk / (ms / 1e3) / 1e12
+        r = {"kernel": "predict (k_predict, binary32 FFMA)", "bound": "alu", "achieved": ach,
+             "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+             "peak_kind": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+             "work": f"{fpk} FLOP per key x {n} keys"}
+    else:
+        per = {"predict": kb + 4 + pb, "partition": npass * 2 * (kb + 4 + pb),
+               "bucket_bounds": 0, "rounds": kb + 4 + 1, "finalize": 0,
+               "polish": 2 * kb + 5 + 2 * pb, "seam": 0}[stage]
+        ach = n * per / (ms / 1e3) / 1e9
+        r = {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+             "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "peak_kind": f"copy bandwidth, {pk['source']}",
+             "work": f"{per} algorithmic bytes per key x {n} keys"}
+    r["ms"] = ms
+    r["traffic"] = traffic
+    r["traffic_source"] = TRAFFIC_SOURCE if traffic is not None else None
+    return r
+
+
+def path_of(st, n, kb, pb, sort_ms, pk):
+    """The whole sort against the path's algorithmic bytes: four passes over every element (read,
+    place, read back, write) and three more per re-mapped conflict."""
+    w = st["w_size"]
+    b_alg = 4 * n * (kb + pb) + 3 * sum(w[1:-1]) * (kb + pb) if len(w) > 2 else 4 * n * (kb + pb)
+    return {"b_alg_bytes": b_alg, "sort_ms": sort_ms,
+            "frac": b_alg / (sort_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+            "frac_of_8tbs": b_alg / (sort_ms / 1e3) / 1e9 / 8000.0}
+
+
+def _timed_sorts(nns, torch, src, model, precision, opts, reps=2, payload=None, key_type=None):
+    """(median sort ms from the library's stage events, the last run's statistics, the output)."""
+    work = torch.empty_like(src)
+    wp = None if payload is None else torch.empty_like(payload)
+    ms, st = [], None
+    for _ in range(reps):
+        work.copy_(src)
+        if wp is not None:
+            wp.copy_(payload)
+        torch.cuda.synchronize()
+        st = nns.sort(work, wp, model, precision=precision, timing=True, key_type=key_type, **opts)
+        ms.append(st["ms_stage"][7])
+    return statistics.median(ms), st, work, wp
+
+
+def _form_entry(n, ms, st, train_ms=None):
+    e = {"sort_ms": ms, "sort_mkeys_s": n / (ms / 1e3) / 1e6, "rounds": st["t"],
+         "sigma": st["sigma"], "trad_rate": st["trad_rate"], "repaired": st["repaired"],
+         "oversized_buckets": st["oversized_buckets"],
+         "stage_ms": dict(zip(STAGES, st["ms_stage"][:7]))}
+    if train_ms is not None:
+        e["job_ms"] = train_ms + ms
+        e["job_mkeys_s"] = n / ((train_ms + ms) / 1e3) / 1e6
+    return e
+
+
+def _e2e_host(nns, L, torch, host, payload, dtype, arch, train, precision, so, reps=3):
+    """End to end through nnsort_train_sort_host from pinned host arrays: copies in, device
+    training, sort, copies out, all inside the timed call."""
+    import ctypes as C
+    hk = torch.from_numpy(host.view({4: np.int32, 8: np.int64}[host.dtype.itemsize]).copy()).pin_memory()
+    hp = None if payload is None else torch.from_numpy(payload.copy()).pin_memory()
+    to = nns._topts(**arch, **train)
+    sop = nns._sopts(so["m"], so["eps"], so["tau"], precision, so["bucket_log2"], None, None, False,
+                     False, so["polish_blocks"])
+    s = torch.cuda.current_stream()
+    tt = []
+    for k in range(reps + 1):
+        hk.numpy()[:] = host.view(hk.numpy().dtype)
+        if hp is not None:
+            hp.numpy()[:] = payload
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = L.lib().nnsort_train_sort_host(C.c_void_p(hk.data_ptr()),
+                                            None if hp is None else C.c_void_p(hp.data_ptr()),
+                                            host.shape[0], dtype, C.byref(to), C.byref(sop), None,
+                                            None, C.c_void_p(s.cuda_stream))
+        t1 = time.perf_counter()
+        L.check("nnsort_train_sort_host", rc)
+        if k:
+            tt.append(t1 - t0)
+    n = host.shape[0]
+    pb = 0 if payload is None else 4
+    return {"value": n / statistics.median(tt) / 1e6, "unit": "Mkeys/s",
+            "h2d_bytes_per_step": n * (host.dtype.itemsize + pb),
+            "d2h_bytes_per_step": n * (host.dtype.itemsize + pb)}
+
+
+# --------------------------------------------------------------------------- other workloads
+C1_TRAIN = dict(translate="ordbits", sample_n=10_000, steps=100, batch=0, lr=1e-2, seed=0)
+
+
+def leg_c1(nns, W, torch, L, pk, steps=20, warmup=3):
+    """1,000,000 float32 keys U[0,1) (seed 0), keys only; 1-32-1 in binary32 trained on a 1% sample
+    (100 full-batch Adam steps, lr 1e-2). One step = training + sort, each on its own copy."""
+    n, arch = 1_000_000, (1, 32, 0)
+    A = dict(layers=1, h1=32, h2=0)
+    host = W.uniform_f32(n, 0)
+    src = torch.from_numpy(host).cuda()
+    so = tuned(0, n, arch, "fp32")
+    bufs = [src.clone() for _ in range(warmup + steps)]
+    l0 = L.lib().nnsort_launch_count()
+
+    def job(b):
+        model, _ = nns.train(b, **A, **C1_TRAIN)
+        nns.sort(b, None, model, precision="fp32", stats=False, **so)
+    for k in range(warmup):
+        job(bufs[k])
+    torch.cuda.synchronize()
+    l0 = L.lib().nnsort_launch_count()
+    a, b = _ev(torch)
+    a.record()
+    for k in range(steps):
+        job(bufs[warmup + k])
+    b.record()
+    torch.cuda.synchronize()
+    launches = (L.lib().nnsort_launch_count() - l0) / steps
+    ms = a.elapsed_time(b) / steps
+    ref = torch.sort(src).values
+    assert all(torch.equal(bufs[warmup + k], ref) for k in range(steps)), "c1 output differs"
+    model, _ = nns.train(src, **A, **C1_TRAIN)
+    ta, tb = _ev(torch)
+    ta.record()
+    nns.train(src, **A, **C1_TRAIN)
+    tb.record()
+    torch.cuda.synchronize()
+    train_ms = ta.elapsed_time(tb)
+    sms, st, out, _ = _timed_sorts(nns, torch, src, model, "fp32", so, reps=5)
+    assert torch.equal(out, ref)
+    pms, pst, out, _ = _timed_sorts(nns, torch, src, model, "pwl", tuned(0, n, arch, "pwl"), reps=5)
+    assert torch.equal(out, ref)
+    return {"workload": "1,000,000 float32 keys U[0,1) seed 0, keys only; MLP 1-32-1 binary32 "
+                        "trained on the device (1% sample, 100 full-batch Adam steps, lr 1e-2)",
+            "value": n / ms / 1e3, "unit": "Mkeys/s", "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "precision": "fp32", "sort_opts": so, "train_ms": train_ms,
+            "launches_per_step": launches,
+            "bound": "launch and latency: the 4 MB input and every buffer fit in L2, so the HBM "
+                     "roofline fraction is not a meaningful bound here",
+            "sort": _form_entry(n, sms, st), "compiled_form": _form_entry(n, pms, pst),
+            "path": path_of(st, n, 4, 0, sms, pk),
+            "e2e": _e2e_host(nns, L, torch, host, None, 0, A, C1_TRAIN, "fp32", so),
+            "parity": "every timed output equals torch.sort of the input (bit for bit)"}
+
+
+C3_ARCH = dict(layers=2, h1=32, h2=32)
+C3_TRAIN = dict(translate="ordbits", sample_n=1_048_576, steps=200, batch=65536, lr=1e-2, seed=0)
+
+
+def leg_c3(nns, W, torch, L, pk, steps=5, warmup=3):
+    """67,108,864 uint64 keys from a Zipf(1.1)-weighted mixture of 8 Gaussians over [0, 2^63), each
+    with an int32 payload (its index), stable key-value sort; 1-32-32-1 trained on the device on a
+    1,048,576-key sample (200 Adam steps, mini-batch 65,536, lr 1e-2). One step = training + sort."""
+    n, arch = 1 << 26, (2, 32, 32)
+    keys, payload = W.gauss_mix_u64(n, 3)
+    sk = torch.from_numpy(keys.view(np.int64)).cuda()
+    sp = torch.from_numpy(payload).cuda()
+    prec = fastest_tensor_form(3, n, arch)
+    so = tuned(3, n, arch, prec)
+    bk = [sk.clone() for _ in range(warmup + steps)]
+    bp = [sp.clone() for _ in range(warmup + steps)]
+
+    def job(k, p):
+        model, hist = nns.train(k, key_type="u64", **C3_ARCH, **C3_TRAIN)
+        nns.sort(k, p, model, precision=prec, stats=False, key_type="u64", **so)
+        return hist
+    for k in range(warmup):
+        hist = job(bk[k], bp[k])
+    torch.cuda.synchronize()
+    l0 = L.lib().nnsort_launch_count()
+    a, b = _ev(torch)
+    a.record()
+    for k in range(steps):
+        job(bk[warmup + k], bp[warmup + k])
+    b.record()
+    torch.cuda.synchronize()
+    launches = (L.lib().nnsort_launch_count() - l0) / steps
+    ms = a.elapsed_time(b) / steps
+    flip = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    rv, ri = torch.sort(sk ^ flip, stable=True)
+    rv ^= flip
+    ri = ri.to(torch.int32)
+    for k in range(steps):
+        assert torch.equal(bk[warmup + k], rv) and torch.equal(bp[warmup + k], ri), "c3 differs"
+    del bk, bp
+    ta, tb = _ev(torch)
+    ta.record()
+    model, hist = nns.train(sk, key_type="u64", **C3_ARCH, **C3_TRAIN)
+    tb.record()
+    torch.cuda.synchronize()
+    train_ms = ta.elapsed_time(tb)
+    forms = {}
+    for p_ in dict.fromkeys((prec, "fp32", "pwl")):
+        o = tuned(3, n, arch, p_)
+        fms, fst, out, outp = _timed_sorts(nns, torch, sk, model, p_, o, reps=3, payload=sp,
+                                           key_type="u64")
+        assert torch.equal(out, rv) and torch.equal(outp, ri)
+        forms[p_] = dict(_form_entry(n, fms, fst, train_ms), sort_opts=o)
+        if p_ == prec:
+            st_c, ms_c = fst, fms
+    live = {k_: v for k_, v in zip(STAGES, st_c["ms_stage"][:7])}
+    dom = max(STAGES, key=lambda k_: live[k_])
+    return {"workload": "67,108,864 uint64 keys, mixture of 8 Gaussians (Zipf 1.1 weights, means over "
+                        "[0, 2^63)), int32 payload = index, stable key-value; MLP 1-32-32-1 trained on "
+                        "the device (1,048,576-key sample, 200 Adam steps, batch 65536, lr 1e-2)",
+            "value": n / ms / 1e3, "unit": "Mkeys/s", "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "precision": prec, "sort_opts": so, "train_ms": train_ms,
+            "final_train_loss": float(hist[-1]), "launches_per_step": launches,
+            "forms": forms,
+            "roofline": roofline_of(dom, live[dom], n, 8, 4, prec, arch,
+                                    st_c["partition_passes"], pk),
+            "path": path_of(st_c, n, 8, 4, ms_c, pk),
+            "e2e": _e2e_host(nns, L, torch, keys, payload, 3, C3_ARCH, C3_TRAIN, prec, so, reps=2),
+            "parity": "every timed output equals torch.sort (stable) of the keys; payloads equal "
+                      "its stable permutation"}, model, sk
+
+
+C4_TRAIN = dict(translate="ordbits", steps=100, batch=0, lr=1e-2)
+
+
+def leg_c4(nns, W, torch, L, pk, reps=3):
+    """4,096 float32 arrays, sizes floor(1000 * 1000^U), each from uniform / normal / lognormal /
+    exponential, each with its own 1-16-1 (1% sample, 100 full-batch Adam steps, lr 1e-2): the
+    batched sort (one pipeline pass over every array) against one nnsort_sort call per array, on
+    the same inputs and models."""
+    arrs = [a for _, a in W.batch_arrays(4096, seed=4)]
+    sizes = [a.shape[0] for a in arrs]
+    total = int(sum(sizes))
+    src = torch.from_numpy(np.concatenate(arrs)).cuda()
+    del arrs
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    views = lambda t: [t[offs[j]:offs[j + 1]] for j in range(len(sizes))]  # noqa: E731
+    sv = views(src)
+    ta, tb = _ev(torch)
+    ta.record()
+    models = [nns.train(v, layers=1, h1=16, h2=0, sample_n=max(1, v.numel() // 100), seed=j,
+                        **C4_TRAIN)[0] for j, v in enumerate(sv)]
+    tb.record()
+    torch.cuda.synchronize()
+    train_ms = ta.elapsed_time(tb)
+    so = tuned(0, total // len(sizes), (1, 16, 0), "fp32")
+    work = torch.empty_like(src)
+    wv = views(work)
+    refs = [torch.sort(v).values for v in sv]
+
+    def run(batch):
+        work.copy_(src)
+        torch.cuda.synchronize()
+        a, b = _ev(torch)
+        a.record()
+        if batch:
+            nns.sort_batch(wv, models, precision="fp32", stats=False, **so)
+        else:
+            for v, f in zip(wv, models):
+                nns.sort(v, None, f, precision="fp32", stats=False, **so)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+    out = {}
+    for label, batch, k in (("batch", True, reps), ("loop", False, max(1, reps - 1))):
+        run(batch)  # warm-up
+        l0 = L.lib().nnsort_launch_count()
+        ms = [run(batch) for _ in range(k)]
+        launches = (L.lib().nnsort_launch_count() - l0) / k
+        assert all(torch.equal(o, r) for o, r in zip(wv, refs)), f"c4 {label} output differs"
+        out[label] = {"ms": statistics.median(ms), "mkeys_s": total / (statistics.median(ms) / 1e3) / 1e6,
+                      "launches": launches}
+    st = nns.sort_batch(wv, models, precision="fp32", **so)
+    sig = [s_["sigma"][0] for s_ in st if s_["t"]]
+    return {"workload": "4,096 float32 arrays, sizes log-uniform in [1K, 1M] (seed 4), each uniform / "
+                        "normal / lognormal / exponential, per-array MLP 1-16-1 (1% sample, 100 Adam "
+                        "steps, lr 1e-2)",
+            "arrays": len(sizes), "keys": total, "value": out["batch"]["mkeys_s"], "unit": "Mkeys/s",
+            "batch": out["batch"], "loop_one_call_per_array": out["loop"],
+            "batch_speedup": out["loop"]["ms"] / out["batch"]["ms"], "sort_opts": so,
+            "train_ms_all_models": train_ms, "sigma_1_median": float(np.median(sig)) if sig else None,
+            "parity": "every array of both runs equals torch.sort of that array (bit for bit)"}
+
+
+def ablation(nns, torch, src, model, n, kb, arch, key_type, dtype, chosen, pk):
+    """What the learned map gains (Sec. "Experimental Study", Exp-1 and Exp-5): the same pipeline
+    with the linear min-max map F(x) = x (no learning; in the key's value and in its order image),
+    the untrained network (initial weights), the learned network in each form, and a radix sort of
+    every key (no model) -- sigma_1, traditional sorting rate, seam repairs and sort time each."""
+    d, _ = model.describe()
+    if key_type == "u64":
+        flip = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+        fl = src ^ flip
+        vlo = float(int((fl.min() ^ flip).item()) & ((1 << 64) - 1))
+        vhi = float(int((fl.max() ^ flip).item()) & ((1 << 64) - 1))
+        del fl
+    else:
+        vlo, vhi = float(src.min().item()), float(src.max().item())
+    lin_value = nns.Model.create(dtype, 1, 1, 0, [1.0, 0.0, 1.0, 0.0], "value", 0, vlo,
+                                 1.0 / (vhi - vlo) if vhi > vlo else 1.0)
+    lin_order = nns.Model.create(dtype, 1, 1, 0, [1.0, 0.0, 1.0, 0.0], "ordbits", d["lo_bits"],
+                                 d["lo_val"], d["scale"])
+    untrained, _ = nns.train(src, key_type=key_type, layers=arch[0], h1=arch[1], h2=arch[2],
+                             sample_n=max(1, n // 100), steps=0, seed=0)
+    if key_type == "u64":
+        ref = torch.sort(src ^ flip).values ^ flip
+    else:
+        ref = torch.sort(src).values
+    out = {}
+    for label, f, prec, a_ in (("linear map, key value", lin_value, "fp32", (1, 1, 0)),
+                               ("linear map, order image", lin_order, "fp32", (1, 1, 0)),
+                               ("untrained network", untrained, "fp32", arch),
+                               ("learned network, binary32", model, "fp32", arch),
+                               (f"learned network, {chosen}", model, chosen, arch),
+                               ("learned network, compiled", model, "pwl", arch)):
+        o = tuned(dtype, n, arch, prec)
+        ms, st, w, _ = _timed_sorts(nns, torch, src, f, prec, o, reps=2, key_type=key_type)
+        assert torch.equal(w, ref), label
+        out[label] = {"sort_ms": ms, "sort_mkeys_s": n / (ms / 1e3) / 1e6,
+                      "sigma_1": st["sigma"][0] if st["t"] else None, "trad_rate": st["trad_rate"],
+                      "repaired": st["repaired"], "oversized_buckets": st["oversized_buckets"]}
+    work = torch.empty_like(src)
+    ms = []
+    for _ in range(2):
+        work.copy_(src)
+        torch.cuda.synchronize()
+        a, b = _ev(torch)
+        a.record()
+        nns.radix_sort(work, key_type=key_type)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    assert torch.equal(work, ref)
+    out["no model: radix sort of every key (nnsort_radix_sort)"] = {
+        "sort_ms": statistics.median(ms), "sort_mkeys_s": n / (statistics.median(ms) / 1e3) / 1e6}
+    lib_ms, _ = _library_sort_ms(torch, src if key_type != "u64" else src ^ flip)
+    out["context: torch.sort (library radix sort)"] = {"sort_ms": lib_ms,
+                                                        "sort_mkeys_s": n / (lib_ms / 1e3) / 1e6}
+    return out
+
+
+def cpu_info():
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": os.uname().machine}
+
+
+def cpu_sorts(host, cap=16_777_216):
+    """Library CPU sorts of a bounded sample of the headline keys on the host cores."""
+    from oracle import oracle as orc
+    sample = np.ascontiguousarray(host[:cap])
+    res = {"sample": f"first {sample.shape[0]} keys of the headline input", **cpu_info()}
+    for label, algo, th in (("std::stable_sort, 1 thread", "stable_sort", 1),
+                            ("std::sort, 1 thread", "sort", 1),
+                            (f"parallel std::sort + merges, {os.cpu_count()} threads", "parallel",
+                             os.cpu_count())):
+        _, dt = orc.cpu_sort(sample, algo, th)
+        res[label] = {"mkeys_s": sample.shape[0] / dt / 1e6, "seconds": dt, "threads": th}
+    return res
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_job(nns, keys, precision, sopts, stats=True, timing=False):
     model, hist = nns.train(keys, **ARCH, **TRAIN)
@@ -406,6 +846,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
+    ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="only the serving loop at its full shape (1,000 requests, 10K..16M keys)")
     ap.add_argument("--experiment", choices=["shift", "quickdraw", "eps"], default=None,
                     help="run one of the paper's experiments instead of the benchmark job")
     args = ap.parse_args()
@@ -434,6 +878,10 @@ def main():
                                "bf16x2" if args.precision == "auto" else args.precision)
         return
     pk = peaks()
+    if args.serve_full:
+        if rank == 0:
+            print(json.dumps({"serving_full": serving_full(nns, W)}), flush=True)
+        return
 
     host = W.lognormal_dup_f32(n, seed=2, sigma=2.0)
     pristine = torch.from_numpy(host).cuda()
@@ -443,11 +891,7 @@ def main():
 
     precision = args.precision
     if precision == "auto":
-        # the tensor-core form the autotuner measured faster on this workload class
-        from paper_1907_08817_gb300 import autotune as AT
-        cands = [(e["sort_ms"], p) for p in ("bf16x2", "bf16")
-                 if (e := AT.tuned_entry(0, n, ARCH["layers"], ARCH["h1"], ARCH["h2"], p)) is not None]
-        precision = min(cands)[1] if cands else "bf16"
+        precision = fastest_tensor_form(0, n, (ARCH["layers"], ARCH["h1"], ARCH["h2"]))
 
     sopts = tuned_sort_opts(precision, n)
     s = torch.cuda.current_stream()
@@ -582,43 +1026,12 @@ def main():
     # roofline of the dominant kernel stage: its mean duration over the timed steps (events the
     # library records on the call's stream)
     kb = 4
-    names = ["predict", "partition", "bucket_bounds", "rounds", "finalize", "polish", "seam"]
+    arch_t = (ARCH["layers"], ARCH["h1"], ARCH["h2"])
     live = [statistics.mean(r[i] for r in timed_stages) for i in range(8)]
     dom = max(range(7), key=lambda i: live[i])
-    npass = st["partition_passes"]
-    alg = {0: n * (kb + 4), 1: npass * n * 2 * (kb + 4), 2: 0, 3: n * (kb + 4 + 1), 4: 0,
-           5: n * (2 * kb + 5), 6: 0}
-    dom_ms = live[dom]
-    tpk = TRAFFIC_PER_KEY.get((names[dom], precision), TRAFFIC_PER_KEY.get((names[dom], None)))
-    traffic = None
-    if tpk is not None:
-        traffic = tpk * n * (npass if dom == 1 else 1)
-    fp32_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-    if dom == 0 and precision in ("bf16", "bf16x2"):
-        # bound by the binary32 work on the CUDA cores around the tensor-core layer
-        ach = n * CUDA_CORE_FLOP_PER_KEY[precision] / (dom_ms / 1e3) / 1e12
-        tens = n * 2 * 64 * 64 * (2 if precision == "bf16x2" else 1) / (dom_ms / 1e3) / 1e12
-        roof = {"kernel": "predict (k_predict_bf16_mg)", "bound": "alu", "achieved": ach,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
-                "tensor": {"achieved": tens, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                           "frac": tens / pk["bf16_tflops"], "peak_source": pk["source"]}}
-    elif dom == 0 and precision == "fp32":
-        ach = n * 2 * (64 + 64 * 64 + 64) / (dom_ms / 1e3) / 1e12
-        roof = {"kernel": "predict (k_predict, binary32 FFMA)", "bound": "alu", "achieved": ach,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
-    else:
-        ach = alg[dom] / (dom_ms / 1e3) / 1e9
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": traffic,
-                "peak_source": pk["source"]}
-    roof["ms"] = dom_ms
-    # the whole sort against the path's algorithmic bytes (4 passes + 3 per re-mapped conflict)
-    w = st["w_size"]
-    b_alg = 4 * n * kb + 3 * sum(w[1:-1]) * kb if len(w) > 2 else 4 * n * kb
-    path = {"b_alg_bytes": b_alg, "sort_ms": sort_ms,
-            "frac_of_hbm": b_alg / (sort_ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+    roof = roofline_of(STAGES[dom], live[dom], n, kb, 0, precision, arch_t, st["partition_passes"], pk)
+    roof["stage_share_of_sort"] = live[dom] / live[7]
+    path = path_of(st, n, kb, 0, sort_ms, pk)
 
     # end to end through the host-array C entry point (pinned host buffers)
     e2e = None
@@ -642,6 +1055,28 @@ def main():
         e2e = {"value": n / statistics.median(tt) / 1e6, "unit": "Mkeys/s",
                "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb}
 
+    # what the learned map gains on the headline input, then the other workloads
+    del bufs
+    abl = None
+    if rank == 0 and not args.no_ablation:
+        abl = {"headline input": ablation(nns, torch, pristine, model, n, kb, arch_t, None, 0,
+                                          precision, pk)}
+    del job
+    configs = None
+    if rank == 0 and not args.no_configs:
+        del pristine
+        torch.cuda.empty_cache()
+        configs = {"1M uniform float32, 1-32-1 binary32": leg_c1(nns, W, torch, L, pk)}
+        c3, c3_model, c3_src = leg_c3(nns, W, torch, L, pk)
+        configs["64M uint64 key-value, 1-32-32-1"] = c3
+        if abl is not None:
+            abl["64M uint64 key-value input"] = ablation(nns, torch, c3_src, c3_model, c3_src.numel(),
+                                                         8, (2, 32, 32), "u64", 3, c3["precision"], pk)
+        del c3_model, c3_src
+        torch.cuda.empty_cache()
+        configs["4,096 float32 arrays, batched vs one call per array"] = leg_c4(nns, W, torch, L, pk)
+        torch.cuda.empty_cache()
+
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serving_leg(nns, W)
@@ -652,7 +1087,8 @@ def main():
         v, dt = oracle_job(ncpu)
         cpu = {"value": v, "unit": "Mkeys/s", "cores": 1, "kind": "oracle",
                "sample": f"{ncpu} keys of the same distribution, same model and recipe "
-                         f"(1% sample, 100 full-batch binary64 steps), {dt:.1f} s"}
+                         f"(1% sample, 100 full-batch binary64 steps), {dt:.1f} s",
+               "host": cpu_info(), "library_sorts": cpu_sorts(host)}
 
     if rank == 0:
         line = {"metric": "Mkeys/s", "value": value, "unit": "Mkeys/s", "n_gpus": ws,
@@ -665,7 +1101,7 @@ def main():
                            "l2": "inputs larger than L2 (each timed step sorts its own 1 GiB copy)"},
                 "roofline": roof, "path": path,
                 "breakdown_ms": {"train": train_ms, "sort": sort_ms,
-                                 **{names[i]: stage[i] for i in range(7)}},
+                                 **{STAGES[i]: stage[i] for i in range(7)}},
                 "sort_only_mkeys_s": n / (sort_ms / 1e3) / 1e6,
                 "stats": {"rounds": st["t"], "w_size": st["w_size"], "sigma": st["sigma"],
                           "e": st["e"], "trad_rate": st["trad_rate"], "buckets": st["buckets"],
@@ -673,7 +1109,8 @@ def main():
                           "repair_ranges": st["repair_ranges"],
                           "final_train_loss": float(hist[-1])},
                 "plain": plain, "other_tensor_form": other, "compiled_form": compiled,
-                "slot_error": slot_error, "serving": serving, "cpu_baseline": cpu, "e2e": e2e,
+                "slot_error": slot_error, "ablation": abl, "configs": configs,
+                "serving": serving, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(),
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)

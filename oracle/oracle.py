@@ -25,12 +25,35 @@ _DT = {np.dtype(np.float32): F32, np.dtype(np.float64): F64,
        np.dtype(np.uint32): U32, np.dtype(np.uint64): U64}
 
 
+_CPU_SRC = os.path.join(_HERE, "cpu_sorts.cpp")
+_CPU_LIB = os.path.join(_HERE, "libcpusorts.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (no FMA contraction, so binary32 steps are the written ones)."""
+    """Compile liboracle.so with gcc (no FMA contraction, so binary32 steps are the written ones)
+    and the library CPU sorts the benchmark times as a baseline (libcpusorts.so, g++)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
                                "-fno-fast-math", "-o", _LIB, _SRC, "-lm"])
+    if force or not os.path.exists(_CPU_LIB) or os.path.getmtime(_CPU_LIB) < os.path.getmtime(_CPU_SRC):
+        subprocess.check_call(["g++", "-O3", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o",
+                               _CPU_LIB, _CPU_SRC])
     return _LIB
+
+
+def cpu_sort(keys: np.ndarray, algo: str, threads: int = 1):
+    """(sorted copy, seconds) of a library CPU sort: 'stable_sort' / 'sort' (std::, one thread) or
+    'parallel' (std::sort of per-thread chunks + parallel pairwise std::merge over `threads`)."""
+    build()
+    lib_ = C.CDLL(_CPU_LIB)
+    lib_.cpu_sort.restype = C.c_double
+    lib_.cpu_sort.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p, C.c_int, C.c_int]
+    keys = np.ascontiguousarray(keys)
+    out = np.empty_like(keys)
+    code = {np.dtype(np.float32): 0, np.dtype(np.float64): 1, np.dtype(np.uint64): 3}[keys.dtype]
+    dt = lib_.cpu_sort(_p(keys), code, keys.shape[0], _p(out),
+                       {"stable_sort": 0, "sort": 1, "parallel": 2}[algo], threads)
+    return out, float(dt)
 
 
 class Norm(C.Structure):

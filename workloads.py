@@ -210,8 +210,7 @@ def serving_requests(count: int = 1000, seed: int = 5, lo: int = 10_000, hi: int
     kinds = (rng_u64(stream_seed(seed, 2), 0, count) % np.uint64(3)).astype(np.int64)
     gaps = -np.log1p(-_unit_f64(rng_u64(stream_seed(seed, 3), 0, count))) / rate_per_s
     arrivals = np.cumsum(gaps)
-    reqs = []
-    for j in range(count):
+    def one(j):
         n = int(sizes[j])
         s = stream_seed(seed, 1000 + j)
         if kinds[j] == 0:
@@ -225,8 +224,11 @@ def serving_requests(count: int = 1000, seed: int = 5, lo: int = 10_000, hi: int
             which = (rng_u64(stream_seed(s, 8), 0, n) % np.uint64(16)).astype(np.int64)
             keys = centres[which] + _normal_f64(stream_seed(s, 9), 0, n)
             kind = "clustered"
-        reqs.append({"arrival_s": float(arrivals[j]), "kind": kind, "keys": keys.astype(np.float64)})
-    return reqs
+        return {"arrival_s": float(arrivals[j]), "kind": kind, "keys": keys.astype(np.float64)}
+    if count > 8 and _threads() > 1:
+        with cf.ThreadPoolExecutor(_threads()) as ex:
+            return list(ex.map(one, range(count)))
+    return [one(j) for j in range(count)]
 
 
 def shift_mix_f32(n: int, noise_frac: float, seed: int = 6, mu: float = 0.5,
