@@ -229,6 +229,7 @@ def _main(argv: Iterable[str]) -> None:
         return ks, ms, None, None
 
     big = one(lambda n: W.lognormal_dup_f32(n, 2, sigma=2.0), 1 << 28, (2, 64, 64))
+    c3 = one(lambda n: W.gauss_mix_u64(n, 3), 1 << 26, (2, 32, 32), steps=200)
     cases = [
         # (label, maker, precision); consecutive cases with the same label share the input
         ("lognormal_dup_f32 256M 1-64-64-1", big, "bf16x2"),
@@ -236,8 +237,9 @@ def _main(argv: Iterable[str]) -> None:
         ("lognormal_dup_f32 256M 1-64-64-1", big, "fp32"),
         ("lognormal_dup_f32 256M 1-64-64-1", big, "pwl"),
         ("uniform_f32 1M 1-32-1", one(lambda n: W.uniform_f32(n, 0), 1_000_000, (1, 32, 0)), "fp32"),
-        ("gauss_mix_u64 64M + payload 1-32-1", one(lambda n: W.gauss_mix_u64(n, 3), 1 << 26,
-                                                   (1, 32, 0), steps=200), "fp32"),
+        ("gauss_mix_u64 64M + payload 1-32-32-1", c3, "bf16x2"),
+        ("gauss_mix_u64 64M + payload 1-32-32-1", c3, "fp32"),
+        ("gauss_mix_u64 64M + payload 1-32-32-1", c3, "pwl"),
         ("batch of f32 arrays 1K..1M 1-16-1", batch, "fp32"),
     ]
     only = argv[argv.index("--case") + 1] if "--case" in argv else None

@@ -115,10 +115,12 @@ int ensure_pinned(Workspace *w, size_t bytes, cudaStream_t s) {
 }
 
 size_t part_hist_bytes(uint64_t N) { return align_up(partition_tiles(N) * RADIX_BINS * sizeof(uint16_t), 256); }
+size_t part_chunk_bytes(uint64_t N) { return align_up(partition_chunks(N) * RADIX_BINS * sizeof(uint32_t), 256); }
+size_t part_bytes(uint64_t N) { return part_hist_bytes(N) + part_chunk_bytes(N) + RADIX_BINS * sizeof(uint32_t); }
 
 // scratch of the partition passes over up to N elements
 int ensure_part(Workspace *w, uint64_t N, cudaStream_t s) {
-    const size_t bytes = part_hist_bytes(N) + partition_chunks(N) * RADIX_BINS * sizeof(uint32_t);
+    const size_t bytes = part_bytes(N);
     if (bytes <= w->part_cap) return NNSORT_OK;
     CK(cudaStreamSynchronize(s));
     if (w->part) CK(cudaFree(w->part));
@@ -139,6 +141,7 @@ int ensure_part(Workspace *w, uint64_t N, cudaStream_t s) {
 cudaError_t part_pass(Workspace *w, PartitionArgs a, cudaStream_t s) {
     a.tile_hist = reinterpret_cast<uint16_t *>(w->part);
     a.chunk = reinterpret_cast<uint32_t *>(w->part + part_hist_bytes(a.N));
+    a.bin_total = reinterpret_cast<uint32_t *>(w->part + part_hist_bytes(a.N) + part_chunk_bytes(a.N));
     return launch_partition(a, s);
 }
 
@@ -475,7 +478,7 @@ struct SegIn {
 };
 
 struct Layout {
-    Seg *segs; SegStats *stats; uint32_t *err; uint32_t *hist; uint32_t *bases;
+    Seg *segs; SegStats *stats; uint32_t *err;
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2]; uint32_t *row[2]; uint32_t *out_rows;
     uint8_t *rank; uint8_t *g_flag; uint32_t *g_x, *g_y; uint32_t *bstart;
     OKey *bmax, *carry, *blo, *bhi;
@@ -493,8 +496,6 @@ Layout carve(unsigned char *base, int nseg, uint64_t N, uint32_t NB, int kb, boo
     L.segs = c.take<Seg>(nseg);
     L.stats = c.take<SegStats>(nseg);
     L.err = c.take<uint32_t>(4);
-    L.hist = c.take<uint32_t>(8 * RADIX_BINS);
-    L.bases = c.take<uint32_t>(8 * RADIX_BINS);
     for (int i = 0; i < 2; ++i) {
         L.gs[i] = c.take<uint32_t>(N);
         L.key[i] = c.take<unsigned char>(N * kb);
@@ -629,14 +630,11 @@ void fill_stats(const Seg &s, const SegStats &d, nnsort_stats *st) {
 
 // Stable multi-block radix sort of `total` packed elements: by key (every 8-bit digit of the order
 // image), then, when `gmax` > 0, stably by a group index in [0, gmax] carried alongside (J). K, P, J
-// are ping-pong pairs with the data in index 0 (P nullable, J null when gmax == 0); `glen` lists
-// (group, elements) for the group passes' histograms, staged through the pinned `hp`
-// (4 x RADIX_BINS words). *fin receives the index of the pair holding the result.
-int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void *const K[2],
-                uint32_t *const P[2], uint32_t *const J[2], uint32_t gmax,
-                const std::vector<std::pair<uint32_t, uint64_t>> &glen, uint32_t *hp, int *fin,
-                cudaStream_t s) {
-    auto pass = [&](int p, int si, bool keydig, int shift, int bits, const uint32_t *base) -> int {
+// are ping-pong pairs with the data in index 0 (P nullable, J null when gmax == 0). *fin receives
+// the index of the pair holding the result.
+int sort_packed(Workspace *w, uint64_t total, int kb, int dtype, void *const K[2], uint32_t *const P[2],
+                uint32_t *const J[2], uint32_t gmax, int *fin, cudaStream_t s) {
+    auto pass = [&](int si, bool keydig, int shift, int bits) -> int {
         const int di = si ^ 1;
         PartitionArgs a{};
         a.N = total;
@@ -655,7 +653,6 @@ int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void
         a.key_digits = keydig ? 1 : 0;
         a.shift = shift;
         a.bits = bits;
-        a.digit_base = base;
         a.key_bytes = kb;
         a.dtype = dtype;
         CK(part_pass(w, a, s));
@@ -663,11 +660,8 @@ int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void
     };
     int rc;
     const int npass = kb;  // even, so the key passes end in pair 0
-    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
-    CK(launch_key_hist(K[0], total, kb, dtype, npass, L.hist, s));
-    CK(launch_digit_bases(L.hist, L.bases, npass, s));
     for (int p = 0; p < npass; ++p)
-        if ((rc = pass(p, p & 1, true, 8 * p, 8, L.bases + p * RADIX_BINS))) return rc;
+        if ((rc = pass(p & 1, true, 8 * p, 8))) return rc;
     *fin = 0;
     if (gmax) {
         // group-index passes of at most 9 bits
@@ -675,19 +669,11 @@ int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void
         while ((1ull << gbits) <= (unsigned long long)gmax) ++gbits;
         const int nsp = (gbits + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
         if (nsp > 4) return NNSORT_E_INVALID_ARG;
-        std::memset(hp, 0, sizeof(uint32_t) * 4 * RADIX_BINS);
-        int sh[4], bt[4];
         for (int q = 0, at = 0; q < nsp; ++q) {
-            bt[q] = (gbits - at + (nsp - q) - 1) / (nsp - q);
-            sh[q] = at;
-            at += bt[q];
-            for (const auto &gl : glen)
-                hp[q * RADIX_BINS + ((gl.first >> sh[q]) & ((1u << bt[q]) - 1u))] += (uint32_t)gl.second;
+            const int bt = (gbits - at + (nsp - q) - 1) / (nsp - q);
+            if ((rc = pass(q & 1, false, at, bt))) return rc;
+            at += bt;
         }
-        CK(cudaMemcpyAsync(L.hist, hp, sizeof(uint32_t) * nsp * RADIX_BINS, cudaMemcpyHostToDevice, s));
-        CK(launch_digit_bases(L.hist, L.bases, nsp, s));
-        for (int q = 0; q < nsp; ++q)
-            if ((rc = pass(q, q & 1, false, sh[q], bt[q], L.bases + q * RADIX_BINS))) return rc;
         *fin = nsp & 1;
     }
     return NNSORT_OK;
@@ -697,16 +683,14 @@ int sort_packed(Workspace *w, Layout &L, uint64_t total, int kb, int dtype, void
 // (now free) partition buffers key[0] / pay[0], stable multi-block radix sort by key, then (when
 // the ranges belong to more than one array) by array index, unpacked
 int repair_long_ranges(Workspace *w, Layout &L, SeamRange *hr, uint32_t nr, int kb, int dtype,
-                       bool anypay, uint32_t *hp, cudaStream_t s) {
+                       bool anypay, cudaStream_t s) {
     std::sort(hr, hr + nr, [](const SeamRange &x, const SeamRange &y) {
         return x.seg != y.seg ? x.seg < y.seg : x.lo < y.lo;
     });
     uint64_t total = 0;
-    std::vector<std::pair<uint32_t, uint64_t>> glen;
     for (uint32_t j = 0; j < nr; ++j) {
         hr[j].pad = (uint32_t)total;
         total += hr[j].hi - hr[j].lo;
-        glen.emplace_back(hr[j].seg, hr[j].hi - hr[j].lo);
     }
     if (total < 2) return NNSORT_OK;
     const bool multi = hr[0].seg != hr[nr - 1].seg;
@@ -717,7 +701,7 @@ int repair_long_ranges(Workspace *w, Layout &L, SeamRange *hr, uint32_t nr, int 
     uint32_t *const J[2] = {L.gs[0], L.gs[1]};
     CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, K[0], P[0], multi ? J[0] : nullptr, 0, sms, s));
     int fin = 0, rc;
-    if ((rc = sort_packed(w, L, total, kb, dtype, K, P, J, multi ? hr[nr - 1].seg : 0u, glen, hp, &fin, s)))
+    if ((rc = sort_packed(w, total, kb, dtype, K, P, J, multi ? hr[nr - 1].seg : 0u, &fin, s)))
         return rc;
     CK(launch_seam_pack(L.ranges, nr, L.segs, total, kb, K[fin], P[fin], nullptr, 1, sms, s));
     return NNSORT_OK;  // the next call on this stream waits before it rewrites the staging area
@@ -727,14 +711,12 @@ int repair_long_ranges(Workspace *w, Layout &L, SeamRange *hr, uint32_t nr, int 
 // elements, packed from the partition buffers (pair `src`), sorted by key and then by bucket, and
 // written to their output positions; then their first/last elements for the seam
 int sort_big_buckets(Workspace *w, Layout &L, BigRange *hb, uint32_t nb, int src, int kb, int dtype,
-                     bool anypay, uint32_t *hp, cudaStream_t s) {
+                     bool anypay, cudaStream_t s) {
     std::sort(hb, hb + nb, [](const BigRange &x, const BigRange &y) { return x.lo < y.lo; });
     uint64_t total = 0;
-    std::vector<std::pair<uint32_t, uint64_t>> glen;
     for (uint32_t j = 0; j < nb; ++j) {
         hb[j].off = (uint32_t)total;
         total += hb[j].hi - hb[j].lo;
-        glen.emplace_back(j, hb[j].hi - hb[j].lo);
     }
     CK(cudaMemcpyAsync(L.big, hb, sizeof(BigRange) * nb, cudaMemcpyHostToDevice, s));
     const int sms = sm_count(), o = src ^ 1;
@@ -745,7 +727,7 @@ int sort_big_buckets(Workspace *w, Layout &L, BigRange *hb, uint32_t nb, int src
     CK(launch_big_pack(L.big, nb, L.segs, total, kb, L.key[src], anypay ? L.pay[src] : nullptr, K[0], P[0],
                        nb > 1 ? J[0] : nullptr, 0, sms, s));
     int fin = 0, rc;
-    if ((rc = sort_packed(w, L, total, kb, dtype, K, P, J, nb > 1 ? nb - 1 : 0u, glen, hp, &fin, s)))
+    if ((rc = sort_packed(w, total, kb, dtype, K, P, J, nb > 1 ? nb - 1 : 0u, &fin, s)))
         return rc;
     CK(launch_big_pack(L.big, nb, L.segs, total, kb, nullptr, nullptr, K[fin], P[fin], nullptr, 1, sms, s));
     CK(launch_big_bounds(L.big, nb, L.segs, kb, dtype, L.blo, L.bhi, s));
@@ -801,8 +783,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     const size_t pin_stats = align_up(sizeof(Seg) * nseg, 64);
     const size_t pin_cnt = pin_stats + align_up(sizeof(SegStats) * nseg + 16, 64);
     const size_t pin_rng = pin_cnt + 64;
-    const size_t pin_hist = align_up(pin_rng + sizeof(SeamRange) * (P.N / SEAM_CTA_MAX + 1), 64);
-    const size_t pin_big = align_up(pin_hist + sizeof(uint32_t) * 4 * RADIX_BINS, 64);
+    const size_t pin_big = align_up(pin_rng + sizeof(SeamRange) * (P.N / SEAM_CTA_MAX + 1), 64);
     const size_t pin_pwl = align_up(pin_big + sizeof(BigRange) * (P.N / POLISH_BIG + 1), 64);
     const size_t pin_need = pin_pwl + pwl_bytes + 256;
     if ((rc = ensure_pinned(w, pin_need, s))) return rc;
@@ -826,7 +807,6 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     }
     CK(cudaMemsetAsync(L.stats, 0, sizeof(SegStats) * nseg, s));
     CK(cudaMemsetAsync(L.err, 0, 16, s));
-    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * MAX_PASSES * RADIX_BINS, s));
 
     const bool timing = o.timing && st;
     if (timing && !w->ev[0])
@@ -838,12 +818,10 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     pa.segs = L.segs;
     pa.nseg = nseg;
     pa.total_tiles = P.tiles;
-    pa.plan = P.pp;
     pa.gs = L.gs[0];
     pa.key_copy = single ? nullptr : L.key[0];
     pa.pay_copy = (single || !anypay) ? nullptr : L.pay[0];
     pa.row_init = rows ? L.row[0] : nullptr;
-    pa.hist = L.hist;
     pa.err = L.err;
     pa.key_bytes = kb;
     pa.dtype = dtype;
@@ -857,7 +835,6 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
         CK(e);
     }
     CK(mark(1));
-    CK(launch_digit_bases(L.hist, L.bases, P.pp.npass, s));
     for (int p = 0; p < P.pp.npass; ++p) {
         const int si = p & 1, di = si ^ 1;
         PartitionArgs a{};
@@ -874,7 +851,6 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
         a.key_digits = 0;
         a.shift = P.pp.shift[p];
         a.bits = P.pp.bits[p];
-        a.digit_base = L.bases + p * RADIX_BINS;
         a.key_bytes = kb;
         a.dtype = dtype;
         CK(part_pass(w, a, s));
@@ -961,8 +937,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
             CK(cudaStreamSynchronize(s));
             for (uint32_t j = 0; j < nbig; ++j)
                 if (hb[j].seg >= (uint32_t)nseg || hb[j].lo >= hb[j].hi || hb[j].hi > P.N) return NNSORT_E_STATE;
-            uint32_t *hh = reinterpret_cast<uint32_t *>(w->pinned + pin_hist);
-            if ((rc = sort_big_buckets(w, L, hb, nbig, fi, kb, dtype, anypay, hh, s))) return rc;
+            if ((rc = sort_big_buckets(w, L, hb, nbig, fi, kb, dtype, anypay, s))) return rc;
         }
     }
     CK(mark(6));
@@ -983,8 +958,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
                 const SeamRange r = hr[i];
                 if (r.seg >= (uint32_t)nseg || r.hi > P.segs[r.seg].n || r.lo >= r.hi) return NNSORT_E_STATE;
             }
-            uint32_t *hh = reinterpret_cast<uint32_t *>(w->pinned + pin_hist);
-            if ((rc = repair_long_ranges(w, L, hr, nlong, kb, dtype, anypay, hh, s))) return rc;
+            if ((rc = repair_long_ranges(w, L, hr, nlong, kb, dtype, anypay, s))) return rc;
         }
     }
     CK(mark(7));
@@ -1031,7 +1005,7 @@ size_t nnsort_workspace_bytes(uint64_t n, int32_t dtype, int32_t with_payload, c
     size_t need = 0;
     const bool rows = o.d_fate != nullptr || (o.d_slots != nullptr && with_payload);
     carve(nullptr, 1, n, P.NB, key_bytes_of(dtype), with_payload != 0, rows, &need);
-    return need + part_hist_bytes(n) + partition_chunks(n) * RADIX_BINS * sizeof(uint32_t);
+    return need + part_bytes(n);
 }
 
 int nnsort_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtype, const nnsort_model *f,
@@ -1105,10 +1079,8 @@ int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtyp
     auto layout = [&](unsigned char *base) {
         c = Carve();
         c.base = base;
-        struct { uint32_t *err, *hist, *bases; void *k1; uint32_t *p1; } r;
+        struct { uint32_t *err; void *k1; uint32_t *p1; } r;
         r.err = c.take<uint32_t>(4);
-        r.hist = c.take<uint32_t>(8 * RADIX_BINS);
-        r.bases = c.take<uint32_t>(8 * RADIX_BINS);
         r.k1 = c.take<unsigned char>(n * kb);
         r.p1 = pay ? c.take<uint32_t>(n) : nullptr;
         return r;
@@ -1119,10 +1091,7 @@ int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtyp
     auto L = layout(w->arena);
     w->last_err = L.err;
     CK(cudaMemsetAsync(L.err, 0, 16, s));
-    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
     const int npass = kb;  // 8-bit digits; an even count, so the result ends in the caller's arrays
-    CK(launch_key_hist(d_keys, n, kb, dtype, npass, L.hist, s));
-    CK(launch_digit_bases(L.hist, L.bases, npass, s));
     void *K[2] = {d_keys, L.k1};
     uint32_t *P[2] = {reinterpret_cast<uint32_t *>(d_payload), L.p1};
     for (int p = 0; p < npass; ++p) {
@@ -1135,7 +1104,6 @@ int nnsort_radix_sort(void *d_keys, int32_t *d_payload, uint64_t n, int32_t dtyp
         a.key_digits = 1;
         a.shift = 8 * p;
         a.bits = 8;
-        a.digit_base = L.bases + p * RADIX_BINS;
         a.key_bytes = kb;
         a.dtype = dtype;
         CK(part_pass(w, a, s));
@@ -1224,7 +1192,6 @@ int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_m
     pa.segs = dseg;
     pa.nseg = 1;
     pa.total_tiles = P.tiles;
-    pa.plan = P.pp;
     pa.slots_out = d_slots;
     pa.y_out = d_y;
     pa.err = err;
@@ -1254,14 +1221,12 @@ int nnsort_sample_labels(const void *d_keys, uint64_t n, int32_t dtype, uint64_t
     auto lay = [&](unsigned char *base) {
         c = Carve();
         c.base = base;
-        struct { void *k[2]; uint32_t *r[2]; uint32_t *hist, *bases, *err; Norm *norm; } L;
+        struct { void *k[2]; uint32_t *r[2]; uint32_t *err; Norm *norm; } L;
         L.k[0] = c.take<unsigned char>(S * kb);
         L.k[1] = c.take<unsigned char>(S * kb);
         L.r[0] = c.take<uint32_t>(S);
         L.r[1] = c.take<uint32_t>(S);
-        L.hist = c.take<uint32_t>(8 * RADIX_BINS);
-        L.bases = c.take<uint32_t>(8 * RADIX_BINS);
-            L.err = c.take<uint32_t>(4);
+        L.err = c.take<uint32_t>(4);
         L.norm = c.take<Norm>(1);
         return L;
     };
@@ -1270,11 +1235,8 @@ int nnsort_sample_labels(const void *d_keys, uint64_t n, int32_t dtype, uint64_t
     auto L = lay(w->arena);
     if ((rc = ensure_part(w, S, s))) return rc;
     if ((rc = ensure_pinned(w, 256, s))) return rc;
-    CK(cudaMemsetAsync(L.hist, 0, sizeof(uint32_t) * 8 * RADIX_BINS, s));
     CK(cudaMemsetAsync(L.err, 0, 16, s));
     CK(launch_sample(d_keys, n, kb, dtype, S, rng_h(seed, TAG_SAMPLE), L.k[0], L.r[0], L.err, s));
-    CK(launch_key_hist(L.k[0], S, kb, dtype, npass, L.hist, s));
-    CK(launch_digit_bases(L.hist, L.bases, npass, s));
     for (int p = 0; p < npass; ++p) {
         const int si = p & 1, di = si ^ 1;
         PartitionArgs a{};
@@ -1286,7 +1248,6 @@ int nnsort_sample_labels(const void *d_keys, uint64_t n, int32_t dtype, uint64_t
         a.key_digits = 1;
         a.shift = 8 * p;
         a.bits = 8;
-        a.digit_base = L.bases + p * RADIX_BINS;
         a.key_bytes = kb;
         a.dtype = dtype;
         CK(part_pass(w, a, s));

@@ -38,9 +38,8 @@ PadArch pad_arch(int layers, int h1, int h2);
 size_t padded_param_count(const PadArch &a);
 
 // ---- predict (k_predict.cu)
-// Fills gs (global position per element), optional key / payload / row copies into the element
-// space and the per-pass digit histograms hist[npass][RADIX_BINS]. Also serves nnsort_predict
-// through slots_out / y_out (element space of a single array).
+// Fills gs (global position per element) and optional key / payload / row copies into the element
+// space. Also serves nnsort_predict through slots_out / y_out (element space of a single array).
 // one segment of the compiled piecewise-linear model in the keys' order-image domain (pwl.cu)
 struct PwlEntry {
     unsigned long long thr;  // smallest order image in the segment (0 for the first)
@@ -56,12 +55,10 @@ struct PredictArgs {
     const Seg *segs;
     int nseg;
     uint32_t total_tiles;
-    PassPlan plan;
     uint32_t *gs;            // nullable
     void *key_copy;          // nullable
     uint32_t *pay_copy;      // nullable
     uint32_t *row_init;      // nullable
-    uint32_t *hist;          // nullable
     uint32_t *slots_out;     // nullable
     float *y_out;            // nullable
     uint32_t *err;
@@ -83,9 +80,10 @@ void pwl_key_table(const nnsort_model_desc &d, const std::vector<double> &brk, c
 // ---- partition (k_partition.cu)
 // One pass of the stable digit partition without inter-block waits (reduce, then scan, then
 // scatter): per tile of SC_TILE elements a digit histogram, per chunk of SC_CHUNK tiles the
-// in-chunk exclusive prefixes and chunk totals, the chunk bases over all chunks, then the scatter
-// of every tile to digit_base[d] + its chunk's base + its in-chunk prefix. Same arguments and
-// result as a chained-scan partition, without its look-back state; tile_hist and chunk are scratch.
+// in-chunk exclusive prefixes and chunk totals (and the digit totals), the chunk bases over all
+// chunks and digits, then the scatter of every tile to its chunk's base + its in-chunk prefix.
+// The pass finds its own digit offsets, so no histogram is needed beforehand; tile_hist, chunk and
+// bin_total are scratch.
 constexpr int SC_THREADS = 512;
 constexpr int SC_ITEMS = 8;
 constexpr int SC_TILE = SC_THREADS * SC_ITEMS;  // 4096
@@ -98,19 +96,14 @@ struct PartitionArgs {
     const uint32_t *row_in; uint32_t *row_out;  // nullable
     int key_digits;         // 1: digit from the key's order image, 0: from gs
     int shift, bits;
-    const uint32_t *digit_base;  // [RADIX_BINS] exclusive global offsets of this pass
     uint16_t *tile_hist;    // [tiles * RADIX_BINS] scratch
     uint32_t *chunk;        // [chunks * RADIX_BINS] scratch
+    uint32_t *bin_total;    // [RADIX_BINS] scratch: elements per digit
     int key_bytes, dtype;
 };
 inline uint64_t partition_tiles(uint64_t N) { return (N + SC_TILE - 1) / SC_TILE; }
 inline uint64_t partition_chunks(uint64_t N) { return (partition_tiles(N) + SC_CHUNK - 1) / SC_CHUNK; }
 cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t s);
-// exclusive scans of the per-pass histograms -> digit bases
-cudaError_t launch_digit_bases(const uint32_t *hist, uint32_t *bases, int npass, cudaStream_t s);
-// histogram of key digits for a key sort
-cudaError_t launch_key_hist(const void *keys, uint64_t N, int key_bytes, int dtype, int npass,
-                            uint32_t *hist, cudaStream_t s);
 // bucket starts by binary search over the partitioned global positions
 cudaError_t launch_bucket_bounds(const uint32_t *gs, uint64_t N, uint32_t nb, int wlog,
                                  uint32_t *bstart, cudaStream_t s);

@@ -13,6 +13,7 @@
 // go out through a shared-memory reorder buffer in digit order, so each digit's run leaves as
 // coalesced stores.
 #include <algorithm>
+#include <cstddef>
 #include <type_traits>
 
 #include "common.cuh"
@@ -70,10 +71,11 @@ __global__ void __launch_bounds__(SC_THREADS) k_tile_hist(PartitionArgs a) {
 #pragma unroll
     for (int ww = 0; ww < SC_NW; ++ww) t += h[ww][tid];  // SC_THREADS == RADIX_BINS
     a.tile_hist[(size_t)blockIdx.x * RADIX_BINS + tid] = (uint16_t)t;
+    if (blockIdx.x == 0) a.bin_total[tid] = 0;  // summed by k_chunk_prefix, which runs after
 }
 
 // per chunk of SC_CHUNK tiles: each tile's histogram becomes its exclusive prefix inside the chunk,
-// and the chunk's totals go to chunk[c]
+// the chunk's totals go to chunk[c] and are added to the digit totals
 __global__ void __launch_bounds__(RADIX_BINS) k_chunk_prefix(PartitionArgs a, uint32_t tiles) {
     const uint32_t c = blockIdx.x, d = threadIdx.x;
     const uint32_t t0 = c * SC_CHUNK;
@@ -88,13 +90,22 @@ __global__ void __launch_bounds__(RADIX_BINS) k_chunk_prefix(PartitionArgs a, ui
         run += v[j];
     }
     a.chunk[(size_t)c * RADIX_BINS + d] = run;
+    if (run) atomicAdd(&a.bin_total[d], run);
 }
 
-// chunk totals -> chunk bases, digit_base[d] + the sum over earlier chunks, in place. Block b takes
-// digits [32 b, 32 b + 32); its 32 warps take consecutive groups of chunks (lane = digit, so every
-// load and store of a warp is one 128-byte line)
+// chunk totals -> chunk bases, the digit's base (elements of all smaller digits) plus the sum over
+// earlier chunks, in place. Block b takes digits [32 b, 32 b + 32); its 32 warps take consecutive
+// groups of chunks (lane = digit, so every load and store of a warp is one 128-byte line)
 __global__ void __launch_bounds__(1024) k_chunk_base(PartitionArgs a, uint32_t chunks) {
     __shared__ uint32_t part[32][33];
+    __shared__ uint32_t dbase[RADIX_BINS];
+    __shared__ uint32_t scratch[33];
+    {   // digit bases: exclusive scan of the digit totals (every block scans all of them)
+        const uint32_t v = threadIdx.x < RADIX_BINS ? a.bin_total[threadIdx.x] : 0u;
+        const uint32_t ex = block_excl_sum(v, scratch, nullptr);
+        if (threadIdx.x < RADIX_BINS) dbase[threadIdx.x] = ex;
+        __syncthreads();
+    }
     const int i = threadIdx.x & 31, j = threadIdx.x >> 5;
     const uint32_t d = blockIdx.x * 32 + i;
     const uint32_t G = (chunks + 31) / 32;
@@ -104,7 +115,7 @@ __global__ void __launch_bounds__(1024) k_chunk_base(PartitionArgs a, uint32_t c
     part[j][i] = sum;
     __syncthreads();
     if (j == 0) {
-        uint32_t run = a.digit_base[d];
+        uint32_t run = dbase[d];
         for (int q = 0; q < 32; ++q) {
             const uint32_t x = part[q][i];
             part[q][i] = run;
@@ -124,30 +135,48 @@ namespace {
 struct ScSmem {
     uint16_t cnt[SC_NW][RADIX_BINS];
     uint16_t dsort[SC_TILE];
-    alignas(16) unsigned char buf[SC_TILE * 8];
+    alignas(16) unsigned char buf[1];  // reorder buffer: every carried array, SC_TILE entries each
 };
+constexpr size_t sc_buf_offset() { return offsetof(ScSmem, buf); }
+
+// stable rank of one item per lane inside the warp's counters: the lanes holding the same digit
+// come from one ballot per digit bit (BITS > 0: a compile-time count; 0: a.bits at run time)
+template <int BITS, bool FULL>
+__device__ __forceinline__ uint32_t sc_peers(uint32_t d, bool valid, int bits) {
+    unsigned peers = 0xFFFFFFFFu;
+    if constexpr (!FULL) {
+        // the invalid lanes of a partial tile are told apart by one more ballot
+        peers = __ballot_sync(0xFFFFFFFFu, valid);
+        if (!valid) peers = ~peers;
+    }
+    if constexpr (BITS > 0) {
+#pragma unroll
+        for (int b = 0; b < BITS; ++b) {
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
+    } else {
+        for (int b = 0; b < bits; ++b) {
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
+    }
+    return peers;
+}
 }  // namespace
 
 // per tile: stable rank of every element by digit, then the scatter to its global position through
-// a shared-memory reorder buffer (each digit's run leaves as coalesced stores)
-template <typename W, bool KEYDIG, bool PAY, bool ROW, int MINB>
-__global__ void __launch_bounds__(SC_THREADS, MINB) k_scatter(PartitionArgs a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    ScSmem &S = *reinterpret_cast<ScSmem *>(smraw);
-    __shared__ uint32_t lstart[RADIX_BINS];
-    __shared__ uint32_t gofs[RADIX_BINS];
-    __shared__ uint32_t scratch[33];
-
+// a shared-memory reorder buffer that holds every carried array, so each element's digit and
+// offset are read once and each digit's run leaves as coalesced stores
+template <typename W, bool KEYDIG, bool PAY, bool ROW, int BITS, bool FULL>
+__device__ __forceinline__ void sc_tile(const PartitionArgs &a, ScSmem &S, uint32_t *lstart, uint32_t *gofs,
+                                        uint32_t *scratch, uint32_t tile, uint32_t cnt_tile) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const uint32_t mask = (1u << a.bits) - 1u;
-    for (int i = lane; i < RADIX_BINS; i += 32) S.cnt[w][i] = 0;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t mask = (1u << (BITS > 0 ? BITS : a.bits)) - 1u;
     const uint64_t base = (uint64_t)tile * SC_TILE;
-    const uint32_t cnt_tile = (uint32_t)min((uint64_t)SC_TILE, a.N - base);
     // this tile's global digit offsets: chunk base + in-chunk prefix (read early, used late)
     const uint32_t off_in = (uint32_t)a.chunk[(size_t)(tile / SC_CHUNK) * RADIX_BINS + tid] +
                             (uint32_t)a.tile_hist[(size_t)tile * RADIX_BINS + tid];
-
     uint32_t gsv[SC_ITEMS], pay[SC_ITEMS], row[SC_ITEMS];
     W key[SC_ITEMS];
     uint16_t dig[SC_ITEMS], wr[SC_ITEMS];
@@ -157,7 +186,7 @@ __global__ void __launch_bounds__(SC_THREADS, MINB) k_scatter(PartitionArgs a) {
     for (int r = 0; r < SC_ITEMS; ++r) {
         const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
         const uint64_t e = base + loc;
-        if (loc < cnt_tile) {
+        if (FULL || loc < cnt_tile) {
             key[r] = kin[e];
             if constexpr (!KEYDIG) gsv[r] = a.gs_in[e];
             if constexpr (PAY) pay[r] = a.pay_in[e];
@@ -168,22 +197,11 @@ __global__ void __launch_bounds__(SC_THREADS, MINB) k_scatter(PartitionArgs a) {
 #pragma unroll
     for (int r = 0; r < SC_ITEMS; ++r) {
         const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
-        const bool valid = loc < cnt_tile;
-        uint32_t d = 0xFFFFu;
+        const bool valid = FULL || loc < cnt_tile;
+        uint32_t d = 0;
         if (valid) d = sc_digit<W, KEYDIG>(a, key[r], KEYDIG ? 0u : gsv[r], mask);
         dig[r] = (uint16_t)d;
-        // lanes holding the same digit: one ballot per digit bit (the invalid lanes of a partial
-        // tile are told apart by one more ballot)
-        unsigned peers = 0xFFFFFFFFu;
-        if (cnt_tile != SC_TILE) {
-            peers = __ballot_sync(0xFFFFFFFFu, valid);
-            if (!valid) peers = ~peers;
-        }
-        for (int b = 0; b < a.bits; ++b) {
-            const bool bit = (d >> b) & 1u;
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, bit);
-            peers &= bit ? bal : ~bal;
-        }
+        const unsigned peers = sc_peers<BITS, FULL>(d, valid, a.bits);
         uint32_t c = 0;
         if (valid) c = S.cnt[w][d];
         __syncwarp();
@@ -197,6 +215,7 @@ __global__ void __launch_bounds__(SC_THREADS, MINB) k_scatter(PartitionArgs a) {
     uint32_t total = 0;
     {
         const int d = tid;  // SC_THREADS == RADIX_BINS
+#pragma unroll
         for (int ww = 0; ww < SC_NW; ++ww) {
             const uint32_t c = S.cnt[ww][d];
             S.cnt[ww][d] = (uint16_t)total;
@@ -207,36 +226,66 @@ __global__ void __launch_bounds__(SC_THREADS, MINB) k_scatter(PartitionArgs a) {
     lstart[tid] = ls;
     gofs[tid] = off_in - ls;
     __syncthreads();
-    uint16_t lpos[SC_ITEMS];
+    W *bk = reinterpret_cast<W *>(S.buf);
+    uint32_t *bg = reinterpret_cast<uint32_t *>(bk + SC_TILE);
+    uint32_t *bp = bg + (KEYDIG ? 0 : SC_TILE);
+    uint32_t *br = bp + (PAY ? SC_TILE : 0);
 #pragma unroll
     for (int r = 0; r < SC_ITEMS; ++r) {
         const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
-        if (loc < cnt_tile) {
+        if (FULL || loc < cnt_tile) {
             const uint32_t d = dig[r];
-            lpos[r] = (uint16_t)(lstart[d] + S.cnt[w][d] + wr[r]);
-            S.dsort[lpos[r]] = (uint16_t)d;
+            const uint32_t lp = lstart[d] + S.cnt[w][d] + wr[r];
+            S.dsort[lp] = (uint16_t)d;
+            bk[lp] = key[r];
+            if constexpr (!KEYDIG) bg[lp] = gsv[r];
+            if constexpr (PAY) bp[lp] = pay[r];
+            if constexpr (ROW) br[lp] = row[r];
         }
     }
-    auto emit = [&](auto *vals, auto *out) {
-        using T = typename std::remove_pointer<decltype(out)>::type;
-        T *b = reinterpret_cast<T *>(S.buf);
-#pragma unroll
-        for (int r = 0; r < SC_ITEMS; ++r) {
-            const uint32_t loc = (uint32_t)w * (32 * SC_ITEMS) + r * 32 + lane;
-            if (loc < cnt_tile) b[lpos[r]] = (T)vals[r];
-        }
-        __syncthreads();
-        for (uint32_t i = tid; i < cnt_tile; i += SC_THREADS) {
-            const uint32_t d = S.dsort[i];
-            out[(size_t)(uint32_t)(gofs[d] + i)] = b[i];
-        }
-        __syncthreads();
-    };
     __syncthreads();
-    emit(key, reinterpret_cast<W *>(a.key_out));
-    if constexpr (!KEYDIG) emit(gsv, a.gs_out);
-    if constexpr (PAY) emit(pay, a.pay_out);
-    if constexpr (ROW) emit(row, a.row_out);
+    W *ko = reinterpret_cast<W *>(a.key_out);
+#pragma unroll 4
+    for (uint32_t i = tid; i < (FULL ? (uint32_t)SC_TILE : cnt_tile); i += SC_THREADS) {
+        const size_t o = (uint32_t)(gofs[S.dsort[i]] + i);
+        ko[o] = bk[i];
+        if constexpr (!KEYDIG) a.gs_out[o] = bg[i];
+        if constexpr (PAY) a.pay_out[o] = bp[i];
+        if constexpr (ROW) a.row_out[o] = br[i];
+    }
+}
+
+template <typename W, bool KEYDIG, bool PAY, bool ROW, int BITS, int MINB>
+__global__ void __launch_bounds__(SC_THREADS, MINB) k_scatter(PartitionArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ScSmem &S = *reinterpret_cast<ScSmem *>(smraw);
+    __shared__ uint32_t lstart[RADIX_BINS];
+    __shared__ uint32_t gofs[RADIX_BINS];
+    __shared__ uint32_t scratch[33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = lane; i < RADIX_BINS; i += 32) S.cnt[w][i] = 0;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t cnt_tile = (uint32_t)min((uint64_t)SC_TILE, a.N - (uint64_t)tile * SC_TILE);
+    if (cnt_tile == SC_TILE)
+        sc_tile<W, KEYDIG, PAY, ROW, BITS, true>(a, S, lstart, gofs, scratch, tile, cnt_tile);
+    else
+        sc_tile<W, KEYDIG, PAY, ROW, BITS, false>(a, S, lstart, gofs, scratch, tile, cnt_tile);
+}
+
+template <typename W, bool KD, bool P, bool R, int MB>
+static cudaError_t sc_launch(const PartitionArgs &a, uint64_t tiles, cudaStream_t s) {
+    const size_t smem = sc_buf_offset() +
+                        (size_t)SC_TILE * (sizeof(W) + (KD ? 0 : 4) + (P ? 4 : 0) + (R ? 4 : 0));
+    auto go = [&](auto kfn) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kfn<<<(unsigned)tiles, SC_THREADS, smem, s>>>(a);
+        return nns_launched(cudaGetLastError());
+    };
+    // the ballot loop unrolled for the digit widths the passes use (9 and 8 bits); others at run time
+    if (a.bits == 9) return go(k_scatter<W, KD, P, R, 9, MB>);
+    if (a.bits == 8) return go(k_scatter<W, KD, P, R, 8, MB>);
+    return go(k_scatter<W, KD, P, R, 0, MB>);
 }
 
 template <typename W, bool KD>
@@ -249,23 +298,13 @@ static cudaError_t sc_go(const PartitionArgs &a, cudaStream_t s) {
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
     k_chunk_base<<<RADIX_BINS / 32, 1024, 0, s>>>(a, (uint32_t)chunks);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
-    const size_t smem = sizeof(ScSmem);
     const bool pay = a.pay_in != nullptr, row = a.row_in != nullptr;
-#define NNS_SC(P, R, MB)                                                                          \
-    {                                                                                             \
-        auto kfn = k_scatter<W, KD, P, R, MB>;                                                    \
-        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
-        if (e != cudaSuccess) return e;                                                           \
-        kfn<<<(unsigned)tiles, SC_THREADS, smem, s>>>(a);                                         \
-        return nns_launched(cudaGetLastError());                                                  \
-    }
     // two resident blocks per SM where the element's registers allow it (4-byte keys)
     constexpr int MB = sizeof(W) == 4 ? 2 : 1;
-    if (pay && row) NNS_SC(true, true, 1)
-    if (pay) NNS_SC(true, false, MB)
-    if (row) NNS_SC(false, true, MB)
-    NNS_SC(false, false, MB)
-#undef NNS_SC
+    if (pay && row) return sc_launch<W, KD, true, true, 1>(a, tiles, s);
+    if (pay) return sc_launch<W, KD, true, false, MB>(a, tiles, s);
+    if (row) return sc_launch<W, KD, false, true, MB>(a, tiles, s);
+    return sc_launch<W, KD, false, false, MB>(a, tiles, s);
 }
 
 cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t s) {
@@ -273,49 +312,6 @@ cudaError_t launch_partition(const PartitionArgs &a, cudaStream_t s) {
     if (a.key_bytes == 4)
         return a.key_digits ? sc_go<uint32_t, true>(a, s) : sc_go<uint32_t, false>(a, s);
     return a.key_digits ? sc_go<uint64_t, true>(a, s) : sc_go<uint64_t, false>(a, s);
-}
-
-// exclusive scan of each pass's histogram (one block per pass)
-__global__ void k_digit_bases(const uint32_t *hist, uint32_t *bases) {
-    __shared__ uint32_t scratch[33];
-    const int p = blockIdx.x;
-    const uint32_t v = hist[p * RADIX_BINS + threadIdx.x];
-    bases[p * RADIX_BINS + threadIdx.x] = block_excl_sum(v, scratch, nullptr);
-}
-
-cudaError_t launch_digit_bases(const uint32_t *hist, uint32_t *bases, int npass, cudaStream_t s) {
-    if (npass <= 0) return cudaSuccess;
-    k_digit_bases<<<npass, RADIX_BINS, 0, s>>>(hist, bases);
-    return nns_launched(cudaGetLastError());
-}
-
-// 8-bit key-digit histograms for every pass of a key sort
-template <typename W>
-__global__ void k_key_hist(const W *keys, uint64_t N, int dtype, int npass, uint32_t *hist) {
-    __shared__ uint32_t h[8 * RADIX_BINS];
-    for (int i = threadIdx.x; i < npass * RADIX_BINS; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t u = ordbits(word64(keys[i]), dtype);
-        for (int p = 0; p < npass; ++p) atomicAdd(&h[p * RADIX_BINS + ((u >> (8 * p)) & 0xFFu)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < npass * RADIX_BINS; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[i], h[i]);
-}
-
-cudaError_t launch_key_hist(const void *keys, uint64_t N, int key_bytes, int dtype, int npass,
-                            uint32_t *hist, cudaStream_t s) {
-    if (N == 0) return cudaSuccess;
-    const int grid = (int)std::min<uint64_t>((N + 255) / 256, 1024);
-    if (key_bytes == 4)
-        k_key_hist<uint32_t><<<grid, 256, 0, s>>>(reinterpret_cast<const uint32_t *>(keys), N, dtype,
-                                                  npass, hist);
-    else
-        k_key_hist<uint64_t><<<grid, 256, 0, s>>>(reinterpret_cast<const uint64_t *>(keys), N, dtype,
-                                                  npass, hist);
-    return nns_launched(cudaGetLastError());
 }
 
 // bstart[b] = first element whose global position is >= b * W (binary search; gs is sorted by

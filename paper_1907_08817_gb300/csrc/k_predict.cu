@@ -2,8 +2,7 @@
 // w <- translate(A), w_pos <- w.map(f), pos <- round(w_pos * m), for every key, in binary32.
 //
 // One pass over the keys (128-bit friendly striped loads), the model's parameters staged once per
-// block in shared memory, the position written as a global position gs = gs_base + pos, and the
-// digit histograms of the bucket-partition passes accumulated in shared memory on the way.
+// block in shared memory, the position written as a global position gs = gs_base + pos.
 #include "common.cuh"
 #include "internal.h"
 
@@ -28,11 +27,8 @@ __device__ __forceinline__ int seg_of_tile(const Seg *segs, int nseg, uint32_t t
 template <int H1, int H2, typename W>
 __global__ void __launch_bounds__(PRED_THREADS) k_predict(PredictArgs a) {
     extern __shared__ __align__(16) float sp[];  // padded parameters
-    __shared__ uint32_t sh_hist[MAX_PASSES * RADIX_BINS];
     __shared__ int sh_seg;
     const int tid = threadIdx.x;
-    const int npass = a.hist ? a.plan.npass : 0;
-    for (int i = tid; i < npass * RADIX_BINS; i += blockDim.x) sh_hist[i] = 0;
     int loaded = -1;
     uint32_t err = 0;
     constexpr int P = (H2 == 0) ? (3 * H1 + 1) : (2 * H1 + H2 * H1 + 2 * H2 + 1);
@@ -75,18 +71,9 @@ __global__ void __launch_bounds__(PRED_THREADS) k_predict(PredictArgs a) {
             if (a.row_init) a.row_init[e] = (uint32_t)i;
             if (a.slots_out) a.slots_out[e] = slot;
             if (a.y_out) a.y_out[e] = y;
-#pragma unroll
-            for (int p = 0; p < MAX_PASSES; ++p) {
-                if (p >= npass) break;
-                const uint32_t d = (g >> a.plan.shift[p]) & ((1u << a.plan.bits[p]) - 1u);
-                atomicAdd(&sh_hist[p * RADIX_BINS + d], 1u);
-            }
         }
     }
     if (err) atomicOr(a.err, err);
-    __syncthreads();
-    for (int i = tid; i < npass * RADIX_BINS; i += blockDim.x)
-        if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
 }
 
 template <int H1, int H2>

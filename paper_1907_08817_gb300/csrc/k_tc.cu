@@ -201,10 +201,9 @@ __host__ __device__ constexpr int tc_ncol(int H, int KPT) {
     return KPT * H <= 32 ? 32 : (KPT * H <= 64 ? 64 : (KPT * H <= 128 ? 128 : 256));
 }
 template <int H, bool SPLIT, int KPT>
-__host__ __device__ constexpr size_t tc_smem_bytes(int npass) {
+__host__ __device__ constexpr size_t tc_smem_bytes() {
     return (size_t)KPT * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)(SPLIT ? 2 : 1) * H * H * 2 +
-           (size_t)TC_M * 16 * 2 + (size_t)H * 16 * 2 + (size_t)(4 * H + 4) * 4 +
-           (size_t)npass * RADIX_BINS * 4;
+           (size_t)TC_M * 16 * 2 + (size_t)H * 16 * 2 + (size_t)(4 * H + 4) * 4;
 }
 
 template <int H, typename W, bool SPLIT, int KPT>
@@ -224,14 +223,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     unsigned char *sBias = sOnes + TC_M * 16 * 2;                     // H x 16 bf16
     float *pf = reinterpret_cast<float *>(sBias + H * 16 * 2);      // W1 | b1 | b2 | W3 | b3
     const float4 *pv = reinterpret_cast<const float4 *>(pf);
-    uint32_t *sh_hist = reinterpret_cast<uint32_t *>(pf + 4 * H + 4);
     __shared__ __align__(8) unsigned long long bar;
     __shared__ uint32_t tmem_base;
     __shared__ int sh_seg;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int npass = a.hist ? a.plan.npass : 0;
-    for (int i = tid; i < npass * RADIX_BINS; i += TC_THREADS) sh_hist[i] = 0;
     if (warp == 0) tmem_alloc<NCOL>(smem_u32(&tmem_base));
     if (tid == 0) {
         mbar_init(smem_u32(&bar), 1);
@@ -448,12 +444,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
             if (a.row_init) a.row_init[e] = (uint32_t)i;
             if (a.slots_out) a.slots_out[e] = slot[g];
             if (a.y_out) a.y_out[e] = y[g];
-#pragma unroll
-            for (int p = 0; p < MAX_PASSES; ++p) {
-                if (p >= npass) break;
-                const uint32_t d = (gpos >> a.plan.shift[p]) & ((1u << a.plan.bits[p]) - 1u);
-                atomicAdd(&sh_hist[p * RADIX_BINS + d], 1u);
-            }
         }
     }
     if (err) atomicOr(a.err, err);
@@ -464,8 +454,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_bf16(PredictArgs a) {
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_free<NCOL>(tbase);
-    for (int i = tid; i < npass * RADIX_BINS; i += TC_THREADS)
-        if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -495,10 +483,9 @@ __device__ __forceinline__ bool grp_or(int id, bool v) {
 }
 
 template <int H, bool SPLIT, int NG>
-__host__ __device__ constexpr size_t tcmg_smem_bytes(int npass) {
+__host__ __device__ constexpr size_t tcmg_smem_bytes() {
     return (size_t)NG * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)(SPLIT ? 2 : 1) * H * H * 2 +
-           (size_t)TC_M * 16 * 2 + (size_t)H * 16 * 2 + (size_t)(4 * H + 4) * 4 +
-           (size_t)npass * RADIX_BINS * 4;
+           (size_t)TC_M * 16 * 2 + (size_t)H * 16 * 2 + (size_t)(4 * H + 4) * 4;
 }
 
 template <int H, typename W, bool SPLIT, int NG>
@@ -517,14 +504,11 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
     unsigned char *sBias = sOnes + TC_M * 16 * 2;                     // H x 16 bf16
     float *pf = reinterpret_cast<float *>(sBias + H * 16 * 2);      // W1 | b1 | b2 | W3 | b3
     const float4 *pv = reinterpret_cast<const float4 *>(pf);
-    uint32_t *sh_hist = reinterpret_cast<uint32_t *>(pf + 4 * H + 4);
     __shared__ __align__(8) unsigned long long bar[NG];
     __shared__ uint32_t tmem_base;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int grp = tid / TC_THREADS, gt = tid % TC_THREADS;
-    const int npass = a.hist ? a.plan.npass : 0;
-    for (int i = tid; i < npass * RADIX_BINS; i += NG * TC_THREADS) sh_hist[i] = 0;
     if (warp == 0) tmem_alloc<NCOL>(smem_u32(&tmem_base));
     if (tid == 0) {
         for (int g = 0; g < NG; ++g) mbar_init(smem_u32(&bar[g]), 1);
@@ -673,12 +657,6 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
         if (a.row_init) a.row_init[e] = (uint32_t)i;
         if (a.slots_out) a.slots_out[e] = slot;
         if (a.y_out) a.y_out[e] = y;
-#pragma unroll
-        for (int p = 0; p < MAX_PASSES; ++p) {
-            if (p >= npass) break;
-            const uint32_t d = (gpos >> a.plan.shift[p]) & ((1u << a.plan.bits[p]) - 1u);
-            atomicAdd(&sh_hist[p * RADIX_BINS + d], 1u);
-        }
     }
     if (err) atomicOr(a.err, err);
     // an MMA whose completion was not seen may still be running: wait for it (bounded) before the
@@ -688,15 +666,12 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_free<NCOL>(tbase);
-    for (int i = tid; i < npass * RADIX_BINS; i += NG * TC_THREADS)
-        if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
 }
 
 template <int H, bool SPLIT>
 static cudaError_t bf16_mg_go(const PredictArgs &p, int sms, cudaStream_t s) {
     const uint64_t n_sub = (uint64_t)p.total_tiles * (PRED_TILE / TC_M);
-    const int npass = p.hist ? p.plan.npass : 0;
-    const size_t smem = tcmg_smem_bytes<H, SPLIT, TC_NG>(npass);
+    const size_t smem = tcmg_smem_bytes<H, SPLIT, TC_NG>();
     const int grid = (int)std::min<uint64_t>((n_sub + TC_NG - 1) / TC_NG, (uint64_t)sms);
     if (grid == 0) return cudaSuccess;
     auto k4 = k_predict_bf16_mg<H, uint32_t, SPLIT, TC_NG>;
@@ -712,13 +687,12 @@ static cudaError_t bf16_mg_go(const PredictArgs &p, int sms, cudaStream_t s) {
 template <int H, bool SPLIT, int KPT>
 static cudaError_t bf16_go(const PredictArgs &p, int sms, cudaStream_t s) {
     const uint64_t subtiles = (uint64_t)p.total_tiles * (PRED_TILE / (KPT * TC_M));
-    const int npass = p.hist ? p.plan.npass : 0;
     // resident blocks per SM: bounded by tensor memory (512 columns) and by shared memory (228 KB,
     // 1 KB reserved per block); the request is raised so that shared memory never admits more
     // blocks than tensor memory can serve (a block waiting in tcgen05.alloc would hold its slot)
     constexpr int NCOL = tc_ncol(H, KPT);
     const int by_tmem = std::min(512 / NCOL, 2048 / TC_THREADS);
-    size_t smem = tc_smem_bytes<H, SPLIT, KPT>(npass);
+    size_t smem = tc_smem_bytes<H, SPLIT, KPT>();
     const size_t floor_req = (size_t)(228 * 1024) / (size_t)(by_tmem + 1) - 1024 + 64;
     smem = std::max(smem, floor_req);
     const int by_smem = (int)((size_t)(228 * 1024) / (smem + 1024));

@@ -29,8 +29,7 @@ constexpr uint64_t NA_MAX_CHUNKS = (NA_MAX_TILES + SC_CHUNK - 1) / SC_CHUNK;
 constexpr size_t NA_PER_ELEM = 2 * 4 + 2 * 8 + 2 * 4 + 1 + 1 + 2 * 4;  // gs, keys, payload, rank,
                                                                       // flag, two index lists
 constexpr size_t NA_BYTES = NA_MAX_N * NA_PER_ELEM + (size_t)NA_MAX_BUCKETS * (4 + 2 * MAXR * 16 + 32) +
-                            NA_MAX_TILES * RADIX_BINS * 2 + NA_MAX_CHUNKS * RADIX_BINS * 4 +
-                            2 * MAX_PASSES * RADIX_BINS * 4 +
+                            NA_MAX_TILES * RADIX_BINS * 2 + NA_MAX_CHUNKS * RADIX_BINS * 4 + RADIX_BINS * 4 +
                             (size_t)(NA_MAX_BUCKETS + 1) * sizeof(SeamRange) + 64 * 1024;
 
 // the scratch: one per device that loads the library, held until the process exits
@@ -55,12 +54,12 @@ thread_local int g_na_cuda = 0;
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct NaLayout {
-    Seg *seg; SegStats *stats; uint32_t *err, *hist, *bases;
+    Seg *seg; SegStats *stats; uint32_t *err;
     uint32_t *gs[2]; void *key[2]; uint32_t *pay[2];
     uint8_t *rank, *flag; uint32_t *gx, *gy, *bstart;
     OKey *bmax, *carry, *blo, *bhi;
     SeamRange *ranges; uint32_t *seam_cnt;
-    uint16_t *tile_hist; uint32_t *chunk;
+    uint16_t *tile_hist; uint32_t *chunk, *bin_total;
     size_t end;
 };
 
@@ -71,8 +70,6 @@ NaLayout na_carve(unsigned char *b) {
     L.seg = reinterpret_cast<Seg *>(take(sizeof(Seg)));
     L.stats = reinterpret_cast<SegStats *>(take(sizeof(SegStats)));
     L.err = reinterpret_cast<uint32_t *>(take(16));
-    L.hist = reinterpret_cast<uint32_t *>(take(4 * MAX_PASSES * RADIX_BINS));
-    L.bases = reinterpret_cast<uint32_t *>(take(4 * MAX_PASSES * RADIX_BINS));
     for (int i = 0; i < 2; ++i) {
         L.gs[i] = reinterpret_cast<uint32_t *>(take(4 * NA_MAX_N));
         L.key[i] = take(8 * NA_MAX_N);
@@ -91,6 +88,7 @@ NaLayout na_carve(unsigned char *b) {
     L.seam_cnt = reinterpret_cast<uint32_t *>(take(16));
     L.tile_hist = reinterpret_cast<uint16_t *>(take(2 * NA_MAX_TILES * RADIX_BINS));
     L.chunk = reinterpret_cast<uint32_t *>(take(4 * NA_MAX_CHUNKS * RADIX_BINS));
+    L.bin_total = reinterpret_cast<uint32_t *>(take(4 * RADIX_BINS));
     L.end = o;
     return L;
 }
@@ -180,15 +178,12 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     NA_CK(cudaMemcpyAsync(L.seg, &sg, sizeof(Seg), cudaMemcpyHostToDevice, s));
     NA_CK(cudaMemsetAsync(L.stats, 0, sizeof(SegStats), s));
     NA_CK(cudaMemsetAsync(L.err, 0, 16, s));
-    NA_CK(cudaMemsetAsync(L.hist, 0, 4 * MAX_PASSES * RADIX_BINS, s));
 
     PredictArgs pa{};
     pa.segs = L.seg;
     pa.nseg = 1;
     pa.total_tiles = sg.ntiles;
-    pa.plan = pp;
     pa.gs = L.gs[0];
-    pa.hist = L.hist;
     pa.err = L.err;
     pa.key_bytes = kb;
     pa.dtype = dtype;
@@ -200,7 +195,6 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
         if (e == cudaErrorNotSupported) return NNSORT_E_UNSUPPORTED;
         NA_CK(e);
     }
-    NA_CK(launch_digit_bases(L.hist, L.bases, pp.npass, s));
     for (int p = 0; p < pp.npass; ++p) {
         const int si = p & 1, di = si ^ 1;
         PartitionArgs a{};
@@ -215,9 +209,9 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
         }
         a.shift = pp.shift[p];
         a.bits = pp.bits[p];
-        a.digit_base = L.bases + p * RADIX_BINS;
         a.tile_hist = L.tile_hist;
         a.chunk = L.chunk;
+        a.bin_total = L.bin_total;
         a.key_bytes = kb;
         a.dtype = dtype;
         NA_CK(launch_partition(a, s));

@@ -190,10 +190,7 @@ __global__ void __launch_bounds__(PRED_THREADS) k_predict_pwl(PredictArgs a) {
     const uint32_t S = a.pwl.S;
     float4 *cf = reinterpret_cast<float4 *>(sraw);  // Ah, Al, Ch, Cl (16-byte entries first)
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(cf + S);
-    __shared__ uint32_t sh_hist[MAX_PASSES * RADIX_BINS];
     const int tid = threadIdx.x;
-    const int npass = a.hist ? a.plan.npass : 0;
-    for (int i = tid; i < npass * RADIX_BINS; i += blockDim.x) sh_hist[i] = 0;
     for (uint32_t i = tid; i < S; i += blockDim.x) {
         const PwlEntry e = a.pwl.tab[i];
         thr[i] = e.thr;
@@ -257,18 +254,9 @@ __global__ void __launch_bounds__(PRED_THREADS) k_predict_pwl(PredictArgs a) {
             if (a.row_init) a.row_init[i] = (uint32_t)i;
             if (a.slots_out) a.slots_out[i] = slot;
             if (a.y_out) a.y_out[i] = __fdiv_rn(__fsub_rn(__fadd_rn(yh, yl), 0.5f), sg.nm_hi);
-#pragma unroll
-            for (int p2 = 0; p2 < MAX_PASSES; ++p2) {
-                if (p2 >= npass) break;
-                const uint32_t dg = (g >> a.plan.shift[p2]) & ((1u << a.plan.bits[p2]) - 1u);
-                atomicAdd(&sh_hist[p2 * RADIX_BINS + dg], 1u);
-            }
         }
     }
     if (err) atomicOr(a.err, err);
-    __syncthreads();
-    for (int i = tid; i < npass * RADIX_BINS; i += blockDim.x)
-        if (sh_hist[i]) atomicAdd(&a.hist[i], sh_hist[i]);
 }
 
 cudaError_t launch_predict_pwl(const PredictArgs &p, int sms, cudaStream_t s) {
