@@ -229,6 +229,20 @@ int nnsort_sample_labels(const void *d_keys, uint64_t n, int32_t dtype, uint64_t
  * h_loss (nullable, `steps` floats) receives the loss before each step. Synchronous. */
 int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_train_opts *o,
                  nnsort_model **out, float *h_loss, cudaStream_t stream);
+/* Trains `count` models at once, model j on the device array d_keys[j] (host array of device
+ * pointers) of ns[j] keys, with the recipe of nnsort_train and seed o->seed + j; model j's sample
+ * size is sample_ns[j] (nullable: o->sample_n for every model). One thread block per model draws
+ * the sample, sorts it, labels it and runs all `steps` Adam steps on chip, so the whole batch is
+ * one launch per sample-size class. Needs one hidden layer of at most 32 units (o->layers == 1,
+ * o->h1 <= 32), no monotone constraint, and 1 <= sample size <= NNSORT_TRAIN_BLOCK_MAX_S; else
+ * NNSORT_E_UNSUPPORTED. out[j] receives model j (free each with nnsort_model_free); h_loss
+ * (nullable, count x steps floats, model-major) the losses. Errors as nnsort_train (NaN in a
+ * sample: NNSORT_E_NAN_KEY, no model is returned). Synchronous. The paper trains one model; this
+ * is the batched form the per-array models of a batch of sorts need. */
+#define NNSORT_TRAIN_BLOCK_MAX_S 16384
+int nnsort_train_batch(void *const *d_keys, const uint64_t *ns, int32_t count, int32_t dtype,
+                       const nnsort_train_opts *o, const uint64_t *sample_ns, nnsort_model **out,
+                       float *h_loss, cudaStream_t stream);
 /* Forward pass of a ReLU MLP with parameters d_params (layout above) on d_x[n] -> d_y[n]. */
 int nnsort_mlp_forward(const float *d_params, int32_t layers, int32_t h1, int32_t h2,
                        const float *d_x, uint64_t n, float *d_y, cudaStream_t stream);

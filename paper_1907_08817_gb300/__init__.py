@@ -15,7 +15,7 @@ from . import _lib as L
 from ._lib import (F32, F64, U32, U64, ORDBITS, VALUE, PREC_BF16, PREC_FP32, LOSS_HUBER,
                    LOSS_MSE, NNSortError)
 
-__all__ = ["Model", "train", "sample_labels", "predict", "sort", "sort_batch", "sort_host", "radix_sort",
+__all__ = ["Model", "train", "train_batch", "sample_labels", "predict", "sort", "sort_batch", "sort_host", "radix_sort",
            "mlp_forward", "mlp_backward", "mlp_loss_grad", "NNSortMLPFunction", "NNSortError",
            "key_code", "release", "workspace_bytes", "stream_status", "version"]
 
@@ -176,6 +176,27 @@ def train(keys, *, key_type=None, layers=1, h1=32, h2=0, translate="ordbits", lo
         _ptr(keys), keys.numel(), key_code(keys, key_type), C.byref(o), C.byref(h),
         hist.ctypes.data_as(C.c_void_p), _stream(stream)))
     return Model(h), hist[:steps]
+
+
+def train_batch(keys_list, *, sample_ns=None, key_type=None, layers=1, h1=16, h2=0,
+                translate="ordbits", loss="mse", huber_delta=0.01, sample_n=10_000, steps=100,
+                batch=0, lr=1e-2, beta1=0.9, beta2=0.999, adam_eps=1e-8, seed=0, stream=None):
+    """Trains one model per array of keys_list in one pass (nnsort_train_batch): model j from its
+    own seeded sample (sample_ns[j] keys, or sample_n) with seed seed + j. Returns (models, losses
+    as a count x steps numpy array)."""
+    cnt = len(keys_list)
+    o = _topts(layers=layers, h1=h1, h2=h2, translate=translate, loss=loss,
+               huber_delta=huber_delta, sample_n=sample_n, steps=steps, batch=batch, lr=lr,
+               beta1=beta1, beta2=beta2, adam_eps=adam_eps, seed=seed, monotone=0)
+    kp = (C.c_void_p * cnt)(*[k.data_ptr() for k in keys_list])
+    ns = (C.c_uint64 * cnt)(*[k.numel() for k in keys_list])
+    sp = None if sample_ns is None else (C.c_uint64 * cnt)(*[int(v) for v in sample_ns])
+    hs = (C.c_void_p * cnt)()
+    hist = np.zeros((cnt, max(steps, 1)), dtype=np.float32)
+    code = key_code(keys_list[0], key_type) if cnt else F32
+    L.check("nnsort_train_batch", L.lib().nnsort_train_batch(
+        kp, ns, cnt, code, C.byref(o), sp, hs, hist.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return [Model(C.c_void_p(h)) for h in hs], hist[:, :steps]
 
 
 def sample_labels(keys, S: int, seed: int = 0, translate="ordbits", key_type=None, stream=None):

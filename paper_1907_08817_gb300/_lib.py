@@ -117,6 +117,7 @@ def lib():
         "nnsort_launch_count": (u64, []),
         "nnsort_sort_noalloc": (C.c_int, [P, P, u64, i32, P, P, P, P]),
         "nnsort_radix_sort": (C.c_int, [P, P, u64, i32, P]),
+        "nnsort_train_batch": (C.c_int, [P, P, i32, i32, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -142,7 +143,7 @@ def exported_symbols() -> list[str]:
             "nnsort_train",
             "nnsort_mlp_forward", "nnsort_mlp_backward", "nnsort_mlp_loss_grad",
             "nnsort_predict", "nnsort_sort", "nnsort_sort_host", "nnsort_sort_batch",
-            "nnsort_train_sort_host", "nnsort_launch_count", "nnsort_sort_noalloc", "nnsort_radix_sort",
+            "nnsort_train_sort_host", "nnsort_launch_count", "nnsort_sort_noalloc", "nnsort_radix_sort", "nnsort_train_batch",
             "nnsort_default_server_opts", "nnsort_server_create", "nnsort_server_submit",
             "nnsort_server_poll", "nnsort_server_wait", "nnsort_server_destroy"]
 

@@ -1325,6 +1325,128 @@ static void init_params_host(int layers, int h1, int h2, uint64_t seed, float *p
     q[HL] = 0.0f;
 }
 
+static_assert(NNSORT_TRAIN_BLOCK_MAX_S == TB_MAX_S, "header and kernel agree on the sample limit");
+
+static bool block_trainable(const nnsort_train_opts &o, uint64_t S) {
+    return o.layers == 1 && o.h1 >= 1 && o.h1 <= 32 && !o.monotone && S >= 1 && S <= TB_MAX_S;
+}
+
+int nnsort_train_batch(void *const *d_keys, const uint64_t *ns, int32_t count, int32_t dtype,
+                       const nnsort_train_opts *op, const uint64_t *sample_ns, nnsort_model **out,
+                       float *h_loss, cudaStream_t s) {
+    nnsort_train_opts o;
+    if (op) o = *op; else nnsort_default_train_opts(&o);
+    if (count < 0 || (count > 0 && (!d_keys || !ns || !out)) || !dtype_ok(dtype)) return NNSORT_E_INVALID_ARG;
+    if (!arch_ok(o.layers, o.h1, o.h2) || o.loss < 0 || o.loss > 1) return NNSORT_E_INVALID_ARG;
+    if (count == 0) return NNSORT_OK;
+    std::vector<uint64_t> S(count), N(count), K(count);
+    for (int j = 0; j < count; ++j) {
+        S[j] = sample_ns ? sample_ns[j] : o.sample_n;
+        N[j] = ns[j];
+        K[j] = reinterpret_cast<uint64_t>(d_keys[j]);
+        if (!d_keys[j] || ns[j] == 0) return NNSORT_E_INVALID_ARG;
+        if (!block_trainable(o, S[j])) return NNSORT_E_UNSUPPORTED;
+        out[j] = nullptr;
+    }
+    const PadArch pa = pad_arch(1, o.h1, 0);
+    const size_t Pp = padded_param_count(pa), P = param_count(1, o.h1, 0);
+    const int steps = (int)o.steps;
+    // models by sample-size class, so each launch's shared sort buffer fits its largest sample
+    const uint32_t caps[3] = {1024, 4096, TB_MAX_S};
+    std::vector<uint32_t> ids;
+    uint32_t first[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 3; ++c) {
+        first[c] = (uint32_t)ids.size();
+        for (int j = 0; j < count; ++j)
+            if (S[j] <= caps[c] && (c == 0 || S[j] > caps[c - 1])) ids.push_back((uint32_t)j);
+    }
+    first[3] = (uint32_t)ids.size();
+    // one device block: tables, outputs, bias corrections, error word
+    const size_t off_n = (size_t)count * 8, off_s = off_n + (size_t)count * 8, off_ids = off_s + (size_t)count * 8;
+    const size_t off_c = align_up(off_ids + (size_t)count * 4, 16);
+    const size_t off_par = align_up(off_c + (size_t)std::max(steps, 1) * 8, 16);
+    const size_t off_norm = align_up(off_par + (size_t)count * Pp * 4, 16);
+    const size_t off_loss = align_up(off_norm + (size_t)count * sizeof(Norm), 16);
+    const size_t off_err = align_up(off_loss + (h_loss ? (size_t)count * steps * 4 : 0), 16);
+    const size_t total = off_err + 16;
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data(), K.data(), (size_t)count * 8);
+    std::memcpy(host.data() + off_n, N.data(), (size_t)count * 8);
+    std::memcpy(host.data() + off_s, S.data(), (size_t)count * 8);
+    std::memcpy(host.data() + off_ids, ids.data(), (size_t)count * 4);
+    for (int t = 0; t < steps; ++t) {
+        const float c1 = (float)(1.0 - std::pow((double)o.beta1, (double)(t + 1)));
+        const float c2 = (float)(1.0 - std::pow((double)o.beta2, (double)(t + 1)));
+        std::memcpy(host.data() + off_c + (size_t)t * 4, &c1, 4);
+        std::memcpy(host.data() + off_c + (size_t)(steps + t) * 4, &c2, 4);
+    }
+    unsigned char *dev = nullptr;
+    CK(cudaMallocAsync((void **)&dev, total, s));
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), off_par, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev + off_err, 0, 16, s);
+    TrainBlockArgs a{};
+    a.keys = reinterpret_cast<const void *const *>(dev);
+    a.n = reinterpret_cast<const uint64_t *>(dev + off_n);
+    a.S = reinterpret_cast<const uint64_t *>(dev + off_s);
+    a.dtype = dtype;
+    a.translate = o.translate;
+    a.h1 = o.h1;
+    a.seed0 = o.seed;
+    a.steps = steps;
+    a.batch = o.batch;
+    a.loss = o.loss;
+    a.delta = o.huber_delta;
+    a.lr = o.lr; a.b1 = o.beta1; a.b2 = o.beta2; a.eps = o.adam_eps;
+    a.c1 = reinterpret_cast<const float *>(dev + off_c);
+    a.c2 = a.c1 + steps;
+    a.params_out = reinterpret_cast<float *>(dev + off_par);
+    a.norm_out = reinterpret_cast<Norm *>(dev + off_norm);
+    a.loss_out = h_loss ? reinterpret_cast<float *>(dev + off_loss) : nullptr;
+    a.err = reinterpret_cast<uint32_t *>(dev + off_err);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+        uint32_t cap = 2;
+        for (uint32_t i = first[c]; i < first[c + 1]; ++i)
+            while (cap < S[ids[i]]) cap <<= 1;
+        a.ids = reinterpret_cast<const uint32_t *>(dev + off_ids) + first[c];
+        a.cap = cap;
+        e = launch_train_block(a, key_bytes_of(dtype), pa.h1, first[c + 1] - first[c], s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data() + off_par, dev + off_par, total - off_par,
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(dev, s);
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        return NNSORT_E_CUDA;
+    }
+    uint32_t err = 0;
+    std::memcpy(&err, host.data() + off_err, 4);
+    if (err & ERR_NAN) return NNSORT_E_NAN_KEY;
+    if (h_loss) std::memcpy(h_loss, host.data() + off_loss, (size_t)count * steps * 4);
+    std::vector<float> up(P);
+    for (int j = 0; j < count; ++j) {
+        Norm q;
+        std::memcpy(&q, host.data() + off_norm + (size_t)j * sizeof(Norm), sizeof(Norm));
+        nnsort_model_desc d;
+        std::memset(&d, 0, sizeof(d));
+        d.dtype = dtype;
+        d.translate = o.translate;
+        d.layers = 1;
+        d.h1 = o.h1;
+        d.lo_bits = q.lo_bits;
+        d.lo_val = q.lo_val;
+        d.scale = q.scale;
+        const float *pp = reinterpret_cast<const float *>(host.data() + off_par) + (size_t)j * Pp;
+        for (size_t u = 0; u < P; ++u) up[u] = pp[pad_index(1, o.h1, 0, pa, u)];
+        const int rc = nnsort_model_create(&d, up.data(), &out[j]);
+        if (rc) {
+            for (int q2 = 0; q2 < j; ++q2) { nnsort_model_free(out[q2]); out[q2] = nullptr; }
+            return rc;
+        }
+    }
+    return NNSORT_OK;
+}
+
 int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_train_opts *op,
                  nnsort_model **out, float *h_loss, cudaStream_t s) {
     nnsort_train_opts o;

@@ -221,6 +221,29 @@ struct TrainStepArgs {
     const float *mask;    // 1 for real parameters, 0 for padding
 };
 cudaError_t launch_train_step(const PadArch &a, const TrainStepArgs &t, cudaStream_t s);
+// many small models at once, one block per model (k_train_block.cu): one hidden layer of padded
+// width 8, 16 or 32, samples of at most TB_MAX_S keys; the sort buffer holds `cap` keys (a power of
+// two >= every S of the launch)
+constexpr uint32_t TB_MAX_S = 16384;
+struct TrainBlockArgs {
+    const void *const *keys;   // [models] device key arrays
+    const uint64_t *n, *S;     // [models] keys, sample size
+    const uint32_t *ids;       // [blocks] model index of each block
+    uint32_t cap;
+    int dtype, translate, h1;  // h1: real hidden width (<= padded width)
+    uint64_t seed0;            // model m uses seed seed0 + m
+    int steps;
+    uint64_t batch;            // 0: full batch
+    int loss;
+    float delta, lr, b1, b2, eps;
+    const float *c1, *c2;      // [steps] Adam bias corrections 1 - beta^(t+1)
+    float *params_out;         // [models][3 H + 1] padded layout
+    Norm *norm_out;            // [models]
+    float *loss_out;           // nullable [models][steps]
+    uint32_t *err;
+};
+cudaError_t launch_train_block(const TrainBlockArgs &a, int key_bytes, int padded_h, uint32_t blocks,
+                               cudaStream_t s);
 int train_grad_blocks(uint64_t nsamples);
 // forward / backward / loss-grad for explicit arrays (nnsort_mlp_* entry points)
 cudaError_t launch_mlp_forward(const PadArch &a, const float *params, const float *x, uint64_t n,

@@ -159,3 +159,39 @@ def test_trained_model_gains_over_untrained_and_linear():
     assert res["trained"]["sigma"][0] < res["linear"]["sigma"][0]
     assert res["trained"]["sigma"][0] < res["untrained"]["sigma"][0]
     assert res["trained"]["trad_rate"] < res["linear"]["trad_rate"]
+
+
+def test_batched_training_tracks_binary64_training():
+    """nnsort_train_batch (one block per model: sample, sort, labels, every Adam step on chip):
+    model j uses seed seed + j and its own sample size; its normaliser equals the oracle's from the
+    same sample bit for bit, and its loss history and weights follow the oracle's binary64 training
+    of that array to binary32 noise, for float32, float64 and uint64 keys, full batch and
+    minibatch, hidden widths 8, 16 and 32."""
+    arrs = [a for _, a in W.batch_arrays(5, seed=9, lo=2000, hi=400_000)]
+    arrs.append(W.lognormal_dup_f32(1_700_000, 4, sigma=2.0))   # a 16,384-key sample (the limit)
+    arrs.append(W.uniform_f32(900, 3))                          # a 9-key sample
+    cases = [(arrs, [max(9, a.shape[0] // 100) for a in arrs[:-2]] + [16384, 9], 16, 0),
+             ([rs_normal(300_000, 5)], [3000], 8, 64),
+             ([W.gauss_mix_u64(500_000, 3)[0]], [5000], 32, 0)]
+    for arrays, S, h, batch in cases:
+        dks = [to_dev(a)[0] for a in arrays]
+        kt = to_dev(arrays[0])[1]
+        models, hist = nns.train_batch(dks, sample_ns=S, key_type=kt, layers=1, h1=h, steps=100,
+                                       batch=batch, lr=1e-2, seed=5)
+        for j, (a, m, s_j) in enumerate(zip(arrays, models, S)):
+            om, p64, ohist = orc.train(a, 1, h, 0, orc.ORDBITS, sample_n=s_j, steps=100,
+                                       batch=batch, lr=1e-2, seed=5 + j)
+            d, p = m.describe()
+            assert (d["lo_bits"], d["lo_val"], d["scale"]) == (om.norm.lo_bits, om.norm.lo_val,
+                                                              om.norm.scale)
+            assert abs(hist[j][0] - ohist[0]) <= 1e-5 * abs(ohist[0]) + 1e-7
+            np.testing.assert_allclose(hist[j], ohist, rtol=2e-3, atol=1e-6)
+            assert np.max(np.abs(p - p64)) <= 2e-3 * np.abs(p64).max()
+    # two hidden layers are trained by nnsort_train, not in a batch
+    with pytest.raises(nns.NNSortError) as ei:
+        nns.train_batch([to_dev(arrs[0])[0]], layers=2, h1=16, h2=16, sample_n=100)
+    assert ei.value.status == -7
+
+
+def rs_normal(n, seed):
+    return np.random.RandomState(seed).standard_normal(n)
