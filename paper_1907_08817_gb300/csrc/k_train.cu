@@ -255,35 +255,55 @@ __global__ void __launch_bounds__(TR_THREADS) k_grad(GradArgs g) {
 }
 
 // Two hidden layers of width H (32 or 64): the per-chunk work as three register-tiled block
-// products over all threads (C = 64 samples per chunk, 4x4 outputs per thread):
+// products over all threads (C = 64 samples per chunk, 4 x TN outputs per thread):
 //   Z  = b2 + H1 W2^T        (forward, accumulated over j in the oracle's order)
 //   D1 = [H1 > 0] (D2 W2)    (backward), D2 = [Z > 0] gy W3
 //   dW2 += D2^T H1           (kept in registers across the block's chunks)
-// Every sum runs in a fixed order, so the gradient is reproducible.
+// Every operand a thread reads in an inner step is a contiguous run of 4 (or 2) floats, one vector
+// load: the products' left operands are staged transposed (H1^T, D2^T: [unit][sample]) next to
+// the row-major copies the dW2 product reads. Every sum runs in a fixed order, so the gradient is
+// reproducible.
 constexpr int GC = 64;          // samples per chunk
 template <int H> struct GemmSmem {
-    static constexpr int LD = H + 4;  // row stride: 16-byte rows, no bank conflicts
+    static constexpr int LD = H + 4;   // row-major [sample][unit] stride (16-byte rows)
+    static constexpr int LDT = GC + 4; // transposed [unit][sample] stride
     static constexpr int P = 2 * H + H * H + 2 * H + 1;
     static constexpr int OFF_W2T = (P + 3) & ~3;
-    static constexpr int OFF_H1 = OFF_W2T + H * LD;
-    static constexpr int OFF_H2 = OFF_H1 + GC * LD;
-    static constexpr int OFF_D2 = OFF_H2 + GC * LD;
-    static constexpr int OFF_D1 = OFF_D2 + GC * LD;
-    static constexpr int OFF_X = OFF_D1 + GC * LD;
+    static constexpr int OFF_H1 = OFF_W2T + H * LD;     // H1 [s][j]
+    static constexpr int OFF_H1T = OFF_H1 + GC * LD;    // H1^T [j][s]; then D1 [s][j] for gx
+    static_assert(GC * H <= H * LDT, "D1 fits the H1^T buffer");
+    static constexpr int OFF_HD = OFF_H1T + H * LDT;    // H2 [s][k], then D2 [s][k]
+    static constexpr int OFF_D2T = OFF_HD + GC * LD;    // D2^T [k][s]
+    static constexpr int OFF_X = OFF_D2T + H * LDT;
     static constexpr int OFF_GY = OFF_X + GC;
     static constexpr int OFF_L = OFF_GY + GC;
     static constexpr int FLOATS = OFF_L + GC;
 };
 
+template <int TN> struct VecT;
+template <> struct VecT<4> { using T = ulonglong2; };
+template <> struct VecT<2> { using T = unsigned long long; };
+// the TN/2 packed column pairs of a contiguous run of TN floats
+template <int TN>
+__device__ __forceinline__ void load_pairs(const float *p, unsigned long long *b) {
+    if constexpr (TN == 4) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+        b[0] = v.x;
+        b[1] = v.y;
+    } else {
+        b[0] = *reinterpret_cast<const unsigned long long *>(p);
+    }
+}
+
 template <int H>
 __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
     using S = GemmSmem<H>;
-    constexpr int LD = S::LD, P = S::P;
+    constexpr int LD = S::LD, LDT = S::LDT, P = S::P;
     constexpr int TN = H / 16;  // outputs per thread along the width (4 for H = 64, 2 for H = 32)
     static_assert(H == 32 || H == 64, "block-product gradient widths");
     extern __shared__ __align__(16) float sm[];
-    float *sp = sm, *W2T = sm + S::OFF_W2T, *sH1 = sm + S::OFF_H1, *sH2 = sm + S::OFF_H2;
-    float *sD2 = sm + S::OFF_D2, *sD1 = sm + S::OFF_D1, *sX = sm + S::OFF_X, *sGY = sm + S::OFF_GY;
+    float *sp = sm, *W2T = sm + S::OFF_W2T, *sH1 = sm + S::OFF_H1, *sH1T = sm + S::OFF_H1T;
+    float *sHD = sm + S::OFF_HD, *sD2T = sm + S::OFF_D2T, *sX = sm + S::OFF_X, *sGY = sm + S::OFF_GY;
     const int tid = threadIdx.x;
     for (int i = tid; i < P; i += TR_THREADS) sp[i] = g.params[i];
     __syncthreads();
@@ -335,7 +355,9 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
         __syncthreads();
         for (int e = tid; e < GC * H; e += TR_THREADS) {
             const int s = e / H, j = e % H;
-            sH1[s * LD + j] = (s < cn) ? relu_f(__fmaf_rn(W1[j], sX[s], b1[j])) : 0.0f;
+            const float h = (s < cn) ? relu_f(__fmaf_rn(W1[j], sX[s], b1[j])) : 0.0f;
+            sH1[s * LD + j] = h;
+            sH1T[j * LDT + s] = h;
         }
         __syncthreads();
         {   // Z = b2 + H1 W2^T, then H2 = relu(Z)
@@ -347,12 +369,12 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
 #pragma unroll 8
             for (int j = 0; j < H; ++j) {
                 unsigned long long b[TP];
-#pragma unroll
-                for (int q = 0; q < TP; ++q) b[q] = pk2(W2T[j * LD + n0 + 2 * q], W2T[j * LD + n0 + 2 * q + 1]);
+                load_pairs<TN>(W2T + j * LD + n0, b);
+                const float4 a4 = *reinterpret_cast<const float4 *>(sH1T + j * LDT + m0);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float av = sH1[(m0 + i) * LD + j];
-                    const unsigned long long a2 = pk2(av, av);
+                    const unsigned long long a2 = pk2(av[i], av[i]);
 #pragma unroll
                     for (int q = 0; q < TP; ++q) acc[i][q] = fma2_rn(b[q], a2, acc[i][q]);
                 }
@@ -363,8 +385,8 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
                 for (int q = 0; q < TP; ++q) {
                     float z0, z1;
                     upk2(acc[i][q], z0, z1);
-                    sH2[(m0 + i) * LD + n0 + 2 * q] = relu_f(z0);
-                    sH2[(m0 + i) * LD + n0 + 2 * q + 1] = relu_f(z1);
+                    sHD[(m0 + i) * LD + n0 + 2 * q] = relu_f(z0);
+                    sHD[(m0 + i) * LD + n0 + 2 * q + 1] = relu_f(z1);
                 }
         }
         __syncthreads();
@@ -372,7 +394,7 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
             float gy = 0.0f, lv = 0.0f;
             if (tid < cn) {
                 float y = b3;
-                for (int k = 0; k < H; ++k) y = __fmaf_rn(W3[k], sH2[tid * LD + k], y);
+                for (int k = 0; k < H; ++k) y = __fmaf_rn(W3[k], sHD[tid * LD + k], y);
                 if (g.mode == 0) {
                     gy = g.gy[c0 + tid];
                 } else {
@@ -395,9 +417,10 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
         __syncthreads();
         for (int e = tid; e < GC * H; e += TR_THREADS) {
             const int s = e / H, k = e % H;  // k = tid % H on every iteration
-            const float h2 = sH2[s * LD + k];
+            const float h2 = sHD[s * LD + k];
             const float d = (h2 > 0.0f) ? sGY[s] * W3[k] : 0.0f;
-            sD2[s * LD + k] = d;
+            sHD[s * LD + k] = d;
+            sD2T[k * LDT + s] = d;
             pb2 = __fadd_rn(pb2, d);
             pw3 = __fmaf_rn(sGY[s], h2, pw3);
         }
@@ -411,12 +434,12 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
 #pragma unroll 8
             for (int k = 0; k < H; ++k) {
                 unsigned long long b[TP];
-#pragma unroll
-                for (int q = 0; q < TP; ++q) b[q] = pk2(W2[k * H + n0 + 2 * q], W2[k * H + n0 + 2 * q + 1]);
+                load_pairs<TN>(W2 + k * H + n0, b);
+                const float4 a4 = *reinterpret_cast<const float4 *>(sD2T + k * LDT + m0);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float av = sD2[(m0 + i) * LD + k];
-                    const unsigned long long a2 = pk2(av, av);
+                    const unsigned long long a2 = pk2(av[i], av[i]);
 #pragma unroll
                     for (int q = 0; q < TP; ++q) acc[i][q] = fma2_rn(a2, b[q], acc[i][q]);
                 }
@@ -429,8 +452,10 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
                     upk2(acc[i][q], d0, d1);
                     const int c = (m0 + i) * LD + n0 + 2 * q;
                     const float e0 = (sH1[c] > 0.0f) ? d0 : 0.0f, e1 = (sH1[c + 1] > 0.0f) ? d1 : 0.0f;
-                    sD1[c] = e0;
-                    sD1[c + 1] = e1;
+                    if (g.gx) {  // D1 [s][j] (stride H) over the (now free) H1^T buffer
+                        sH1T[(m0 + i) * H + n0 + 2 * q] = e0;
+                        sH1T[(m0 + i) * H + n0 + 2 * q + 1] = e1;
+                    }
                     const float xs = sX[m0 + i];
                     pb1[2 * q] = __fadd_rn(pb1[2 * q], e0);
                     pb1[2 * q + 1] = __fadd_rn(pb1[2 * q + 1], e1);
@@ -441,19 +466,25 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
         __syncthreads();
         if (g.gx && tid < cn) {
             float gx = 0.0f;
-            for (int j = 0; j < H; ++j) gx = __fmaf_rn(sD1[tid * LD + j], W1[j], gx);
+            for (int j = 0; j < H; ++j) gx = __fmaf_rn(sH1T[tid * H + j], W1[j], gx);
             g.gx[c0 + tid] = gx;
         }
         // dW2 += D2^T H1 over this chunk's samples
 #pragma unroll 4
         for (int s = 0; s < cn; ++s) {
             unsigned long long b[TP];
-#pragma unroll
-            for (int q = 0; q < TP; ++q) b[q] = pk2(sH1[s * LD + j0 + 2 * q], sH1[s * LD + j0 + 2 * q + 1]);
+            load_pairs<TN>(sH1 + s * LD + j0, b);
+            float av[TK];
+            if constexpr (TK == 4) {
+                const float4 a4 = *reinterpret_cast<const float4 *>(sHD + s * LD + k0);
+                av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+            } else {
+                const float2 a2v = *reinterpret_cast<const float2 *>(sHD + s * LD + k0);
+                av[0] = a2v.x; av[1] = a2v.y;
+            }
 #pragma unroll
             for (int i = 0; i < TK; ++i) {
-                const float av = sD2[s * LD + k0 + i];
-                const unsigned long long a2 = pk2(av, av);
+                const unsigned long long a2 = pk2(av[i], av[i]);
 #pragma unroll
                 for (int q = 0; q < TP; ++q) aW2[i][q] = fma2_rn(a2, b[q], aW2[i][q]);
             }
@@ -463,7 +494,7 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
     // combine the partial sums (the activation tiles are free now)
     float *R2b = sH1, *R2w = R2b + TR_THREADS, *R1b = R2w + TR_THREADS, *R1w = R1b + TR_THREADS * TN;
     float *Rg = R1w + TR_THREADS * TN, *Rl = Rg + GC;
-    static_assert((2 + 2 * TN) * TR_THREADS + 2 * GC <= 4 * GC * LD, "partials fit the activation tiles");
+    static_assert((2 + 2 * TN) * TR_THREADS + 2 * GC <= GC * LD + H * LDT, "partials fit the activation tiles");
     R2b[tid] = pb2;
     R2w[tid] = pw3;
 #pragma unroll
@@ -489,11 +520,11 @@ __global__ void __launch_bounds__(TR_THREADS, 2) k_grad_gemm(GradArgs g) {
         out[2 * H + H * H + tid] = b;        // b2
         out[3 * H + H * H + tid] = w;        // W3
     } else if (tid < 2 * H) {  // column j of D1: thread (tm, j / TN), slot j % TN, for every tm
-        const int j = tid - H, tn = j / TN, q = j % TN;
+        const int j = tid - H, tn2 = j / TN, q = j % TN;
         float b = 0.0f, w = 0.0f;
         for (int tm2 = 0; tm2 < TR_THREADS / 16; ++tm2) {
-            b = __fadd_rn(b, R1b[(tm2 * 16 + tn) * TN + q]);
-            w = __fadd_rn(w, R1w[(tm2 * 16 + tn) * TN + q]);
+            b = __fadd_rn(b, R1b[(tm2 * 16 + tn2) * TN + q]);
+            w = __fadd_rn(w, R1w[(tm2 * 16 + tn2) * TN + q]);
         }
         out[H + j] = b;                      // b1
         out[j] = w;                          // W1
