@@ -15,7 +15,7 @@ one sort call per array; the serving loop), the ablation of the learned map and 
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --experiment shift|quickdraw|eps   (the paper's Exp-3, Exp-2 stand-in, Exp-4)
-  python bench.py --serve-full                        (the serving loop at its full shape alone)
+  python bench.py --serve-full                        (the serving loop alone)
 """
 from __future__ import annotations
 
@@ -226,7 +226,7 @@ def _serve_once(nns, reqs, scale, workers, max_batch):
     return lats, wall
 
 
-def serving_leg(nns, W, count=300, lo=10_000, hi=16_000_000, repeats=3, seed=5):
+def serving_leg(nns, W, count=1000, lo=10_000, hi=16_000_000, repeats=3, seed=5):
     """float64 requests (log-uniform sizes in [lo, hi]; uniform / lognormal(0,2) / clustered),
     per-request device-trained 1-32-32-1, 120 GiB admission budget. First a saturation run (every
     request submitted at once, continuous batching) gives the saturated request rate; then Poisson
@@ -873,7 +873,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--serve-full", action="store_true",
-                    help="only the serving loop at its full shape (1,000 requests, 10K..16M keys)")
+                    help="only the serving loop (1,000 requests of 10K..16M keys)")
     ap.add_argument("--experiment", choices=["shift", "quickdraw", "eps"], default=None,
                     help="run one of the paper's experiments instead of the benchmark job")
     args = ap.parse_args()

@@ -505,32 +505,37 @@ __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_
                              unsigned long long *mm /*[2 * SNW]*/, uint32_t *scratch /*33*/) {
     static_assert(NBIN % SOLVE_THREADS == 0, "whole bins per thread");
     constexpr int BPT = NBIN / SOLVE_THREADS;
+    using K = decltype(kf(src[0]));  // the key's own unsigned width
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    unsigned long long lo = ~0ull, hi = 0ull;
+    K lo = (K)~(K)0, hi = 0;
     for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
-        const unsigned long long k = kf(src[i]);
+        const K k = kf(src[i]);
         lo = k < lo ? k : lo;
         hi = k > hi ? k : hi;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-        const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+        const K l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        const K h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
         lo = l2 < lo ? l2 : lo;
         hi = h2 > hi ? h2 : hi;
     }
     if (lane == 0) { mm[w] = lo; mm[SNW + w] = hi; }
     for (uint32_t b = tid; b < NBIN; b += SOLVE_THREADS) bins[b] = 0;
     __syncthreads();
-    lo = mm[0];
-    hi = mm[SNW];
+    lo = (K)mm[0];
+    hi = (K)mm[SNW];
 #pragma unroll
     for (int q = 1; q < SNW; ++q) {
-        lo = mm[q] < lo ? mm[q] : lo;
-        hi = mm[SNW + q] > hi ? mm[SNW + q] : hi;
+        lo = (K)mm[q] < lo ? (K)mm[q] : lo;
+        hi = (K)mm[SNW + q] > hi ? (K)mm[SNW + q] : hi;
     }
-    const unsigned long long range = hi - lo;
-    const int sh = range < NBIN ? 0 : (64 - __clzll((long long)range)) - 12;  // (range >> sh) < NBIN
+    const K range = hi - lo;
+    int sh = 0;  // (range >> sh) < NBIN
+    if (range >= NBIN) {
+        if constexpr (sizeof(K) == 8) sh = (64 - __clzll((long long)range)) - 12;
+        else sh = (32 - __clz((int)range)) - 12;
+    }
     for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS)
         atomicAdd(&bins[(uint32_t)((kf(src[i]) - lo) >> sh)], 1u);
     __syncthreads();
@@ -559,13 +564,13 @@ __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_
     // slot, written back to src (whose identity list is no longer needed)
     for (uint32_t j = tid; j < cnt; j += SOLVE_THREADS) {
         const Idx x = dst[j];
-        const unsigned long long kx = kf(x);
+        const K kx = kf(x);
         const uint32_t b = (uint32_t)((kx - lo) >> sh);
         const uint32_t st = b ? bins[b - 1] : 0u, e = bins[b];
         uint32_t r = 0;
         for (uint32_t i = st; i < e; ++i) {
             const Idx y = dst[i];
-            const unsigned long long ky = kf(y);
+            const K ky = kf(y);
             r += (ky < kx || (ky == kx && y < x)) ? 1u : 0u;
         }
         src[st + r] = x;
@@ -592,7 +597,20 @@ struct PolishSmem {
     int seg, t;
 };
 
-template <typename W, typename Idx>
+// order image of a key whose type is known at compile time (FL: IEEE float, else unsigned)
+// (in the key's own width, so that 32-bit keys are compared and binned in 32-bit arithmetic)
+template <typename W, bool FL>
+__device__ __forceinline__ W okey_of(W w) {
+    if constexpr (!FL) {
+        return w;
+    } else if constexpr (sizeof(W) == 4) {
+        return (w & 0x80000000u) ? (W)~w : (W)(w | 0x80000000u);
+    } else {
+        return (w >> 63) ? (W)~w : (W)(w | 0x8000000000000000ull);
+    }
+}
+
+template <typename W, typename Idx, bool FL>
 struct BucketView {
     // element accessors (generic pointers: shared memory on chip, global memory otherwise)
     const W *K;        // keys
@@ -604,9 +622,8 @@ struct BucketView {
     const uint32_t *T;    // rows (nullable)
     Idx *X, *Y, *TB;
     uint32_t wm;
-    int dtype;
     __device__ __forceinline__ uint32_t ls(uint32_t i) const { return S16 ? S16[i] : (G[i] & wm); }
-    __device__ __forceinline__ unsigned long long ok(uint32_t i) const { return ordbits(word64(K[i]), dtype); }
+    __device__ __forceinline__ W ok(uint32_t i) const { return okey_of<W, FL>(K[i]); }
     __device__ __forceinline__ uint32_t tb(uint32_t i) const { return T ? T[i] : i; }
     __device__ __forceinline__ bool less(uint32_t a, uint32_t b) const {
         const unsigned long long ka = ok(a), kb = ok(b);
@@ -618,8 +635,8 @@ struct BucketView {
 // out-of-order split against the running maximum (carry from earlier buckets first); the in-order
 // rest is the run R_r. Sets v.F for leftover elements (last conflict array and out-of-order ones)
 // and counts the out-of-order ones in sm.ooo.
-template <typename W, typename Idx>
-__device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx> &v,
+template <typename W, typename Idx, bool FL>
+__device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx, FL> &v,
                             uint32_t b, uint32_t nbk) {
     const int tid = threadIdx.x;
     const int t = sm.t;
@@ -702,20 +719,20 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
     }
 }
 
-template <typename W, typename Idx>
-__device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx> &v,
+template <typename W, typename Idx, bool FL>
+__device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx, FL> &v,
                               uint32_t b, uint32_t s0, uint32_t nbk, const Seg &sg) {
     const int tid = threadIdx.x;
     const int t = sm.t;
     const int keybits = (a.key_bytes == 4) ? 32 : 64;
-    polish_runs<W, Idx>(a, sm, v, b, nbk);
+    polish_runs<W, Idx, FL>(a, sm, v, b, nbk);
     // The bucket's output -- the leftover (the last conflict array and every out-of-order element)
     // sorted by QuickSort(w) and merged with the in-order runs R_1..R_t of Fig. "Algorithm polish" --
     // is all of its elements in (key, row) order, so it is computed as one stable sort of the whole
     // bucket; the runs above supply the out-of-order counts and the fates.
     for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.X[i] = (Idx)i;
     __syncthreads();
-    auto kf = [&](Idx x) -> unsigned long long { return v.ok(x); };
+    auto kf = [&](Idx x) { return v.ok(x); };
     Idx *A = nbk <= BIN_SORT_MAX ? cta_bin_sort<Idx>(v.X, v.Y, nbk, kf, sm.bins, sm.mm, sm.scratch)
                                  : nullptr;
     if (!A) A = cta_radix_sort<Idx>(v.X, v.Y, nbk, keybits, kf, sm.hist, sm.wcnt, sm.scratch);
@@ -766,7 +783,7 @@ int polish_capacity(int key_bytes, bool payload, bool rows, int wlog, int blocks
     return (int)cap;
 }
 
-template <typename W>
+template <typename W, bool FL>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
     extern __shared__ __align__(16) unsigned char praw[];
     PolishSmem &sm = *reinterpret_cast<PolishSmem *>(praw);
@@ -791,10 +808,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
         // left to the multi-block sort of all such buckets
         if (tid == 0) atomicAdd(&a.stats[sm.seg].oversized, 1u);
         uint32_t *TB = reinterpret_cast<uint32_t *>(dyn);
-        BucketView<W, uint32_t> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
-                                  a.rank + s0, a.g_flag + s0, nullptr, nullptr, a.g_x + s0, a.g_y + s0,
-                                  TB, Wn - 1u, a.dtype};
-        polish_runs<W, uint32_t>(a, sm, v, b, nbk);
+        BucketView<W, uint32_t, FL> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
+                                      a.rank + s0, a.g_flag + s0, nullptr, nullptr, a.g_x + s0,
+                                      a.g_y + s0, TB, Wn - 1u};
+        polish_runs<W, uint32_t, FL>(a, sm, v, b, nbk);
         if (tid < sm.t && sm.ooo[tid]) atomicAdd(&a.stats[sm.seg].ooo[tid], (unsigned long long)sm.ooo[tid]);
         if (tid == 0) {
             BigRange r;
@@ -848,16 +865,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
             }
         }
         __syncthreads();
-        BucketView<W, uint16_t> v{K, S16, nullptr, R, F, P, T, X, Y, TB, Wn - 1u, a.dtype};
-        polish_bucket<W, uint16_t>(a, sm, v, b, s0, nbk, sg);
+        BucketView<W, uint16_t, FL> v{K, S16, nullptr, R, F, P, T, X, Y, TB, Wn - 1u};
+        polish_bucket<W, uint16_t, FL>(a, sm, v, b, s0, nbk, sg);
     } else {
         if (tid == 0) atomicAdd(&a.stats[sm.seg].oversized, 1u);
         uint32_t *TB = reinterpret_cast<uint32_t *>(dyn);
-        BucketView<W, uint32_t> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
-                                  a.rank + s0, a.g_flag + s0, a.pay ? a.pay + s0 : nullptr,
-                                  a.rows ? a.rows + s0 : nullptr, a.g_x + s0, a.g_y + s0,
-                                  TB, Wn - 1u, a.dtype};
-        polish_bucket<W, uint32_t>(a, sm, v, b, s0, nbk, sg);
+        BucketView<W, uint32_t, FL> v{reinterpret_cast<const W *>(a.keys) + s0, nullptr, a.gs + s0,
+                                      a.rank + s0, a.g_flag + s0, a.pay ? a.pay + s0 : nullptr,
+                                      a.rows ? a.rows + s0 : nullptr, a.g_x + s0, a.g_y + s0,
+                                      TB, Wn - 1u};
+        polish_bucket<W, uint32_t, FL>(a, sm, v, b, s0, nbk, sg);
     }
 }
 
@@ -1252,9 +1269,11 @@ cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s) {
 
 template <typename W> static cudaError_t polish_go(const SolveArgs &a, cudaStream_t s) {
     const size_t smem = std::max(a.polish_smem, sizeof(PolishSmem) + 16 + ((size_t)4 << a.wlog));
-    cudaError_t e = cudaFuncSetAttribute(k_polish<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the key's order image with its type fixed at compile time (IEEE float or unsigned)
+    auto kfn = (a.dtype == NNSORT_F32 || a.dtype == NNSORT_F64) ? k_polish<W, true> : k_polish<W, false>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_polish<W><<<a.NB, SOLVE_THREADS, smem, s>>>(a);
+    kfn<<<a.NB, SOLVE_THREADS, smem, s>>>(a);
     return nns_launched(cudaGetLastError());
 }
 cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s) {
