@@ -357,8 +357,8 @@ int nnsort_model_create(const nnsort_model_desc *desc, const float *h_params, nn
 
 int nnsort_model_free(nnsort_model *f) {
     if (!f) return NNSORT_E_INVALID_ARG;
-    if (f->d_params) cudaFree(f->d_params);
-    delete f;
+    if (f->d_params && !f->owner) cudaFree(f->d_params);
+    delete f;  // a shared parameter block is freed with its last model
     return NNSORT_OK;
 }
 
@@ -1382,7 +1382,17 @@ int nnsort_train_batch(void *const *d_keys, const uint64_t *ns, int32_t count, i
     }
     unsigned char *dev = nullptr;
     CK(cudaMallocAsync((void **)&dev, total, s));
-    cudaError_t e = cudaMemcpyAsync(dev, host.data(), off_par, cudaMemcpyHostToDevice, s);
+    // the trained parameters stay where the kernel writes them: one device block that the models
+    // share (each model's padded parameters are a slice; the block is freed with the last model)
+    float *dpar = nullptr;
+    cudaError_t e = cudaMalloc((void **)&dpar, (size_t)count * Pp * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFreeAsync(dev, s);
+        g_last_cuda = (int)e;
+        return NNSORT_E_OOM;
+    }
+    std::shared_ptr<void> block(dpar, [](void *p) { cudaFree(p); });
+    e = cudaMemcpyAsync(dev, host.data(), off_par, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dev + off_err, 0, 16, s);
     TrainBlockArgs a{};
     a.keys = reinterpret_cast<const void *const *>(dev);
@@ -1399,7 +1409,7 @@ int nnsort_train_batch(void *const *d_keys, const uint64_t *ns, int32_t count, i
     a.lr = o.lr; a.b1 = o.beta1; a.b2 = o.beta2; a.eps = o.adam_eps;
     a.c1 = reinterpret_cast<const float *>(dev + off_c);
     a.c2 = a.c1 + steps;
-    a.params_out = reinterpret_cast<float *>(dev + off_par);
+    a.params_out = dpar;
     a.norm_out = reinterpret_cast<Norm *>(dev + off_norm);
     a.loss_out = h_loss ? reinterpret_cast<float *>(dev + off_loss) : nullptr;
     a.err = reinterpret_cast<uint32_t *>(dev + off_err);
@@ -1411,7 +1421,9 @@ int nnsort_train_batch(void *const *d_keys, const uint64_t *ns, int32_t count, i
         a.cap = cap;
         e = launch_train_block(a, key_bytes_of(dtype), pa.h1, first[c + 1] - first[c], s);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data() + off_par, dev + off_par, total - off_par,
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data() + off_par, dpar, (size_t)count * Pp * sizeof(float),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data() + off_norm, dev + off_norm, total - off_norm,
                                               cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(dev, s);
@@ -1438,11 +1450,20 @@ int nnsort_train_batch(void *const *d_keys, const uint64_t *ns, int32_t count, i
         d.scale = q.scale;
         const float *pp = reinterpret_cast<const float *>(host.data() + off_par) + (size_t)j * Pp;
         for (size_t u = 0; u < P; ++u) up[u] = pp[pad_index(1, o.h1, 0, pa, u)];
-        const int rc = nnsort_model_create(&d, up.data(), &out[j]);
-        if (rc) {
+        nnsort_model *f = new (std::nothrow) nnsort_model();
+        if (!f) {
             for (int q2 = 0; q2 < j; ++q2) { nnsort_model_free(out[q2]); out[q2] = nullptr; }
-            return rc;
+            return NNSORT_E_OOM;
         }
+        f->desc = d;
+        f->P = P;
+        f->params = up;
+        f->pad = pa;
+        f->Ppad = Pp;
+        f->d_params = dpar + (size_t)j * Pp;
+        f->owner = block;
+        cudaGetDevice(&f->device);
+        out[j] = f;
     }
     return NNSORT_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -267,4 +268,6 @@ struct nnsort_model {
     size_t P = 0, Ppad = 0;
     float *d_params = nullptr;  // padded layout
     int device = 0;
+    std::shared_ptr<void> owner;  // set when d_params lies in a device block shared by several
+                                  // models (freed with the last of them), else d_params is its own
 };
