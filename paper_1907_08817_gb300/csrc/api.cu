@@ -1478,7 +1478,7 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     const uint64_t B = o.batch ? o.batch : S;
     const PadArch pa = pad_arch(o.layers, o.h1, o.h2);
     const size_t Pp = padded_param_count(pa), P = param_count(o.layers, o.h1, o.h2);
-    const int blocks = train_grad_blocks(B);
+    const int blocks = train_grad_blocks(pa, B);
     // device buffers for this call (separate from the per-stream arena used by sampling)
     float *dx = nullptr;
     const size_t fl = S * 2 + Pp * 5 + (size_t)blocks * Pp + blocks + std::max<uint32_t>(o.steps, 1) + 64;
@@ -1573,7 +1573,7 @@ static int backward_common(const float *d_params, int layers, int h1, int h2, co
     if (!d_gparams || (n && !d_x)) return NNSORT_E_INVALID_ARG;
     PadArch pa = pad_arch(layers, h1, h2);
     const size_t Pp = padded_param_count(pa), P = param_count(layers, h1, h2);
-    const int blocks = train_grad_blocks(n);
+    const int blocks = train_grad_blocks(pa, n);
     float *pp = nullptr, *ex = nullptr;
     int rc = with_padded(d_params, layers, h1, h2, s, &pp, &pa, (size_t)blocks * Pp + blocks + Pp + 4, &ex);
     if (rc) return rc;

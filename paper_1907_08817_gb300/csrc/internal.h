@@ -245,7 +245,7 @@ struct TrainBlockArgs {
 };
 cudaError_t launch_train_block(const TrainBlockArgs &a, int key_bytes, int padded_h, uint32_t blocks,
                                cudaStream_t s);
-int train_grad_blocks(uint64_t nsamples);
+int train_grad_blocks(const PadArch &a, uint64_t nsamples);
 // forward / backward / loss-grad for explicit arrays (nnsort_mlp_* entry points)
 cudaError_t launch_mlp_forward(const PadArch &a, const float *params, const float *x, uint64_t n,
                                float *y, cudaStream_t s);

@@ -545,9 +545,13 @@ template <int H1, int H2> static size_t grad_smem() {
     return sizeof(float) * (((P + 3) & ~3) + TR_CHUNK * (3 + 2 * H1 + 2 * H2e));
 }
 
-int train_grad_blocks(uint64_t nsamples) {
-    // at least one chunk per block; at most 1024 blocks
-    const uint64_t b = (nsamples + 4 * TR_CHUNK - 1) / (4 * TR_CHUNK);
+int train_grad_blocks(const PadArch &a, uint64_t nsamples) {
+    // the block-product kernel (two hidden layers of 32 or 64) takes four chunks per block, so its
+    // thousands of per-block partial gradients stay few; the per-sample kernel of the small shapes
+    // takes one chunk per block, so small batches still spread over the GPU; at most 1024 blocks
+    const bool gemm = a.layers == 2 && (a.h1 == 32 || a.h1 == 64);
+    const uint64_t per = gemm ? 4 * TR_CHUNK : TR_CHUNK;
+    const uint64_t b = (nsamples + per - 1) / per;
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, 1024));
 }
 
@@ -660,7 +664,7 @@ cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, 
 
 cudaError_t launch_train_step(const PadArch &a, const TrainStepArgs &t, cudaStream_t s) {
     const uint64_t B = t.batch ? t.batch : t.S;
-    const int blocks = train_grad_blocks(B);
+    const int blocks = train_grad_blocks(a, B);
     GradArgs g{};
     g.params = t.params; g.x = t.x; g.label = t.label; g.n = B; g.S = t.S;
     g.bseed = t.batch_seed; g.bofs = (uint64_t)t.step * B;
@@ -713,7 +717,7 @@ cudaError_t launch_mlp_backward(const PadArch &a, const float *params, const flo
                                 const float *gy, const float *label, uint64_t n, int mode,
                                 int loss, float delta, float *partials, float *loss_partials,
                                 float *gx, cudaStream_t s, int *blocks_out) {
-    const int blocks = train_grad_blocks(n);
+    const int blocks = train_grad_blocks(a, n);
     if (blocks_out) *blocks_out = blocks;
     GradArgs g{};
     g.params = params; g.x = x; g.gy = gy; g.label = label; g.n = n; g.S = n;
