@@ -455,6 +455,10 @@ int nnsort_stream_status(cudaStream_t s) {
     int rc = get_ws(s, &w);
     if (rc) return rc;
     CK(cudaStreamSynchronize(s));
+    // the training kernels' word (process-wide) holds only the timeout bit
+    uint32_t te = 0;
+    if (uint32_t *tw = train_err_word()) CK(cudaMemcpy(&te, tw, 4, cudaMemcpyDeviceToHost));
+    if (te & ERR_TIMEOUT) return NNSORT_E_TIMEOUT;
     if (!w->last_err) return NNSORT_OK;
     uint32_t e = 0;
     CK(cudaMemcpy(&e, w->last_err, 4, cudaMemcpyDeviceToHost));
@@ -1479,6 +1483,8 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     const PadArch pa = pad_arch(o.layers, o.h1, o.h2);
     const size_t Pp = padded_param_count(pa), P = param_count(o.layers, o.h1, o.h2);
     const int blocks = train_grad_blocks(pa, B);
+    uint32_t *terr = train_err_word();
+    if (!terr) return NNSORT_E_CUDA;
     // device buffers for this call (separate from the per-stream arena used by sampling)
     float *dx = nullptr;
     const size_t fl = S * 2 + Pp * 5 + (size_t)blocks * Pp + blocks + std::max<uint32_t>(o.steps, 1) + 64;
@@ -1522,6 +1528,7 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     t.batch_seed = rng_h(o.seed, TAG_BATCH); t.loss = o.loss; t.delta = o.huber_delta;
     t.lr = o.lr; t.b1 = o.beta1; t.b2 = o.beta2; t.eps = o.adam_eps; t.P = Pp;
     t.mask = o.monotone ? dmask : nullptr;
+    CK(cudaMemsetAsync(terr, 0, sizeof(uint32_t), s));
     for (uint32_t k = 0; k < o.steps; ++k) {
         t.step = (int)k;
         CK(launch_train_step(pa, t, s));
@@ -1530,8 +1537,11 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     CK(cudaMemcpyAsync(hpp.data(), dp, Pp * sizeof(float), cudaMemcpyDeviceToHost, s));
     std::vector<float> hl(std::max<uint32_t>(o.steps, 1));
     if (o.steps) CK(cudaMemcpyAsync(hl.data(), dloss, o.steps * sizeof(float), cudaMemcpyDeviceToHost, s));
+    uint32_t herr = 0;
+    CK(cudaMemcpyAsync(&herr, terr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     cudaFreeAsync(dx, s);
+    if (herr & ERR_TIMEOUT) return NNSORT_E_TIMEOUT;
     if (h_loss) std::memcpy(h_loss, hl.data(), o.steps * sizeof(float));
     std::vector<float> up(P);
     for (size_t u = 0; u < P; ++u) up[u] = hpp[pad_index(o.layers, o.h1, o.h2, pa, u)];

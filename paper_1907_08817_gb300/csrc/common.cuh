@@ -129,6 +129,11 @@ __device__ __forceinline__ unsigned long long add2_rn(unsigned long long a, unsi
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ unsigned long long mul2_rn(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ unsigned long long sub2_rn(unsigned long long a, unsigned long long b) {
     unsigned long long r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -215,6 +220,17 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // comes first, so that a wait ends even if the timer were not to advance), and raises ERR_TIMEOUT
 constexpr unsigned long long SPIN_LIMIT_NS = 4000000000ull;
 constexpr uint32_t SPIN_LIMIT_POLLS = 1u << 26;
+
+// SplitMix64 (Steele, Lea and Flood): draw i of the stream with seed `seed` (training samples and
+// mini-batches)
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t rng_draw(uint64_t seed, uint64_t i) {
+    return mix64(seed + (i + 1) * 0x9E3779B97F4A7C15ull);
+}
 
 // ---------------------------------------------------------------------------------------------
 // block-wide exclusive sum of one u32 per thread (blockDim multiple of 32, <= 1024)

@@ -245,7 +245,30 @@ struct TrainBlockArgs {
 };
 cudaError_t launch_train_block(const TrainBlockArgs &a, int key_bytes, int padded_h, uint32_t blocks,
                                cudaStream_t s);
+// gradient of a sum over samples (k_train.cu, k_train_tc.cu). mode 0: s = sum_i gy_i * y_i (explicit
+// upstream gradient); mode 1: mean loss over the batch with labels; mode 2: as mode 1 with batch
+// indices drawn from the batch stream. Each block (or block group) writes one partial gradient row.
+struct GradArgs {
+    const float *params;
+    const float *x, *gy, *label;
+    uint64_t n;          // samples in the batch
+    uint64_t S;          // labelled set size (mode 2)
+    uint64_t bseed;      // batch stream (mode 2)
+    uint64_t bofs;       // first draw of this step (mode 2)
+    int mode, loss;
+    float delta;
+    float inv_n;
+    float *partials;     // [rows * P]
+    float *loss_partials;  // [rows], nullable
+    float *gx;           // nullable (mode 0)
+};
 int train_grad_blocks(const PadArch &a, uint64_t nsamples);
+// two hidden layers of width 64 on the tensor cores (k_train_tc.cu): blocks of the launch (each
+// writes two partial rows), and the launch; a bounded wait that expired sets ERR_TIMEOUT in the
+// library's training error word (train_err_word)
+int grad_tc64_blocks(uint64_t nsamples);
+cudaError_t launch_grad_tc64(const GradArgs &g, cudaStream_t s);
+uint32_t *train_err_word();
 // forward / backward / loss-grad for explicit arrays (nnsort_mlp_* entry points)
 cudaError_t launch_mlp_forward(const PadArch &a, const float *params, const float *x, uint64_t n,
                                float *y, cudaStream_t s);

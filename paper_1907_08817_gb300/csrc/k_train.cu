@@ -25,15 +25,6 @@ namespace nns {
 constexpr int TR_THREADS = 256;
 constexpr int TR_CHUNK = 64;  // samples whose activations a block stages at once
 
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t rng_draw(uint64_t seed, uint64_t i) {
-    return mix64(seed + (i + 1) * 0x9E3779B97F4A7C15ull);
-}
-
 // ---- sampling
 template <typename W>
 __global__ void k_sample(const W *keys, uint64_t n, int dtype, uint64_t S, uint64_t seed, W *out,
@@ -97,24 +88,7 @@ __global__ void k_mlp_forward(const float *params, const float *x, uint64_t n, f
         y[i] = mlp_fwd_f32<H1, H2>(sp, x[i]);
 }
 
-// ---- gradient of a sum over samples
-// mode 0: s = sum_i gy_i * y_i (explicit upstream gradient); mode 1: mean loss over the batch
-// with labels; mode 2: as mode 1 with batch indices drawn from the batch stream.
-struct GradArgs {
-    const float *params;
-    const float *x, *gy, *label;
-    uint64_t n;          // samples in the batch
-    uint64_t S;          // labelled set size (mode 2)
-    uint64_t bseed;      // batch stream (mode 2)
-    uint64_t bofs;       // first draw of this step (mode 2)
-    int mode, loss;
-    float delta;
-    float inv_n;
-    float *partials;     // [gridDim.x * P]
-    float *loss_partials;  // [gridDim.x]
-    float *gx;           // nullable (mode 0)
-};
-
+// ---- gradient of a sum over samples (GradArgs: internal.h)
 template <int H1, int H2>
 __global__ void __launch_bounds__(TR_THREADS) k_grad(GradArgs g) {
     constexpr int HL = (H2 == 0) ? H1 : H2;
@@ -546,10 +520,12 @@ template <int H1, int H2> static size_t grad_smem() {
 }
 
 int train_grad_blocks(const PadArch &a, uint64_t nsamples) {
-    // the block-product kernel (two hidden layers of 32 or 64) takes four chunks per block, so its
+    // width 64: the tensor-core kernel, two partial rows per block
+    if (a.layers == 2 && a.h1 == 64) return 2 * grad_tc64_blocks(nsamples);
+    // the block-product kernel (two hidden layers of 32) takes four chunks per block, so its
     // thousands of per-block partial gradients stay few; the per-sample kernel of the small shapes
     // takes one chunk per block, so small batches still spread over the GPU; at most 1024 blocks
-    const bool gemm = a.layers == 2 && (a.h1 == 32 || a.h1 == 64);
+    const bool gemm = a.layers == 2 && a.h1 == 32;
     const uint64_t per = gemm ? 4 * TR_CHUNK : TR_CHUNK;
     const uint64_t b = (nsamples + per - 1) / per;
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, 1024));
@@ -586,7 +562,7 @@ static cudaError_t grad_dispatch(const PadArch &a, const GradArgs &g, int blocks
         case 8: return grad_go<8, 8>(g, blocks, s);
         case 16: return grad_go<16, 16>(g, blocks, s);
         case 32: return grad_gemm_go<32>(g, blocks, s);
-        case 64: return grad_gemm_go<64>(g, blocks, s);
+        case 64: return launch_grad_tc64(g, s);
         }
     }
     return cudaErrorInvalidValue;

@@ -29,14 +29,6 @@ namespace {
 constexpr int TB_THREADS = 256;
 constexpr int TB_WARPS = TB_THREADS / 32;
 
-__device__ __forceinline__ uint64_t tb_mix(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t tb_rng(uint64_t seed, uint64_t i) {
-    return tb_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ull);
-}
 __device__ __forceinline__ double tb_unit53(uint64_t u) {
     return __dmul_rn((double)(u >> 11), 1.0 / 9007199254740992.0);
 }
@@ -81,11 +73,11 @@ __global__ void __launch_bounds__(TB_THREADS, H >= 32 ? 1 : 2) k_train_block(Tra
     uint32_t err = 0;
 
     // sample and its order images; the rest of the buffer sorts last
-    const uint64_t ss = tb_rng(seed, 1);
+    const uint64_t ss = rng_draw(seed, 1);
     for (uint32_t i = tid; i < a.cap; i += TB_THREADS) {
         unsigned long long u = ~0ull;
         if (i < S) {
-            const uint64_t r = __umul64hi(tb_rng(ss, i), n);
+            const uint64_t r = __umul64hi(rng_draw(ss, i), n);
             const uint64_t w = word64(keys[r]);
             if (key_is_nan(w, a.dtype)) err |= ERR_NAN;
             u = ordbits(w, a.dtype);
@@ -127,16 +119,16 @@ __global__ void __launch_bounds__(TB_THREADS, H >= 32 ? 1 : 2) k_train_block(Tra
         a.norm_out[m] = q;
         // initial weights: W1_j in (-sqrt 6, sqrt 6), kink c_j in [0, 1) (b1_j = -W1_j c_j),
         // output weights in (-sqrt(6/h1), sqrt(6/h1)), b3 = 0; padding units stay 0
-        const uint64_t si = tb_rng(seed, 2);
+        const uint64_t si = rng_draw(seed, 2);
         uint64_t c = 0;
         const double r1 = __dsqrt_rn(6.0), r3 = __dsqrt_rn(__ddiv_rn(6.0, (double)a.h1));
         for (int u = 0; u < P; ++u) { sp[u] = 0.0f; sm_[u] = 0.0f; sv[u] = 0.0f; }
         for (int j = 0; j < a.h1; ++j)
-            sp[j] = __double2float_rn(__dmul_rn(__dsub_rn(__dmul_rn(2.0, tb_unit53(tb_rng(si, c++))), 1.0), r1));
+            sp[j] = __double2float_rn(__dmul_rn(__dsub_rn(__dmul_rn(2.0, tb_unit53(rng_draw(si, c++))), 1.0), r1));
         for (int j = 0; j < a.h1; ++j)
-            sp[H + j] = __double2float_rn(__dmul_rn(-(double)sp[j], tb_unit53(tb_rng(si, c++))));
+            sp[H + j] = __double2float_rn(__dmul_rn(-(double)sp[j], tb_unit53(rng_draw(si, c++))));
         for (int j = 0; j < a.h1; ++j)
-            sp[2 * H + j] = __double2float_rn(__dmul_rn(__dsub_rn(__dmul_rn(2.0, tb_unit53(tb_rng(si, c++))), 1.0), r3));
+            sp[2 * H + j] = __double2float_rn(__dmul_rn(__dsub_rn(__dmul_rn(2.0, tb_unit53(rng_draw(si, c++))), 1.0), r3));
     }
     __syncthreads();
     // inputs and labels in place of the sorted images
@@ -150,14 +142,14 @@ __global__ void __launch_bounds__(TB_THREADS, H >= 32 ? 1 : 2) k_train_block(Tra
 
     const uint64_t B = a.batch ? a.batch : S;
     const float inv_n = 1.0f / (float)B;
-    const uint64_t bseed = tb_rng(seed, 3);
+    const uint64_t bseed = rng_draw(seed, 3);
     for (int step = 0; step < a.steps; ++step) {
         float g[P];
 #pragma unroll
         for (int u = 0; u < P; ++u) g[u] = 0.0f;
         float lsum = 0.0f;
         for (uint64_t i = tid; i < B; i += TB_THREADS) {
-            const uint64_t src = a.batch ? __umul64hi(tb_rng(bseed, (uint64_t)step * B + i), S) : i;
+            const uint64_t src = a.batch ? __umul64hi(rng_draw(bseed, (uint64_t)step * B + i), S) : i;
             const float2 v = xl[src];
             // hidden activations are recomputed in the backward loop rather than kept in registers
             float y = sp[3 * H];
