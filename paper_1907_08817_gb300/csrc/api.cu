@@ -1487,11 +1487,14 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     if (!terr) return NNSORT_E_CUDA;
     // device buffers for this call (separate from the per-stream arena used by sampling)
     float *dx = nullptr;
-    const size_t fl = S * 2 + Pp * 5 + (size_t)blocks * Pp + blocks + std::max<uint32_t>(o.steps, 1) + 64;
+    const uint32_t nst = std::max<uint32_t>(o.steps, 1);
+    const size_t fl = S * 2 + Pp * 5 + (size_t)blocks * Pp + blocks + nst + 2 * (size_t)nst + 64;
     CK(cudaMallocAsync((void **)&dx, fl * sizeof(float), s));
     float *dlab = dx + S, *dp = dlab + S, *dm = dp + Pp, *dv = dm + Pp, *dg = dv + Pp;
     float *dmask = dg + Pp;
     float *dpart = dmask + Pp, *dlp = dpart + (size_t)blocks * Pp, *dloss = dlp + blocks;
+    float *dc12 = dloss + nst;                                           // [2 * steps]
+    unsigned int *dsync = reinterpret_cast<unsigned int *>(dc12 + 2 * (size_t)nst);  // [2]
     nnsort_model_desc d;
     int rc = nnsort_sample_labels(d_keys, n, dtype, S, o.seed, o.translate, &d, dx, dlab, nullptr, s);
     if (rc) { cudaFreeAsync(dx, s); return rc; }
@@ -1529,9 +1532,21 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     t.lr = o.lr; t.b1 = o.beta1; t.b2 = o.beta2; t.eps = o.adam_eps; t.P = Pp;
     t.mask = o.monotone ? dmask : nullptr;
     CK(cudaMemsetAsync(terr, 0, sizeof(uint32_t), s));
-    for (uint32_t k = 0; k < o.steps; ++k) {
-        t.step = (int)k;
-        CK(launch_train_step(pa, t, s));
+    if (pa.layers == 2 && pa.h1 == 64) {
+        // every step in one cooperative launch (its blocks meet twice per step)
+        std::vector<float> c12(2 * (size_t)nst);
+        for (uint32_t k = 0; k < o.steps; ++k) {
+            c12[k] = (float)(1.0 - std::pow((double)o.beta1, (double)(k + 1)));
+            c12[o.steps + k] = (float)(1.0 - std::pow((double)o.beta2, (double)(k + 1)));
+        }
+        CK(cudaMemcpyAsync(dc12, c12.data(), c12.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(dsync, 0, 2 * sizeof(unsigned int), s));
+        CK(launch_train_tc64(t, o.steps, dc12, dsync, s));
+    } else {
+        for (uint32_t k = 0; k < o.steps; ++k) {
+            t.step = (int)k;
+            CK(launch_train_step(pa, t, s));
+        }
     }
     std::vector<float> hpp(Pp);
     CK(cudaMemcpyAsync(hpp.data(), dp, Pp * sizeof(float), cudaMemcpyDeviceToHost, s));

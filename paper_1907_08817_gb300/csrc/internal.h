@@ -264,10 +264,14 @@ struct GradArgs {
 };
 int train_grad_blocks(const PadArch &a, uint64_t nsamples);
 // two hidden layers of width 64 on the tensor cores (k_train_tc.cu): blocks of the launch (each
-// writes two partial rows), and the launch; a bounded wait that expired sets ERR_TIMEOUT in the
+// writes one partial row), and the launch; a bounded wait that expired sets ERR_TIMEOUT in the
 // library's training error word (train_err_word)
 int grad_tc64_blocks(uint64_t nsamples);
 cudaError_t launch_grad_tc64(const GradArgs &g, cudaStream_t s);
+// every Adam step of a training run of that model in one cooperative launch: c12 = device
+// [2 * steps] bias corrections (1 - beta1^(t+1), then 1 - beta2^(t+1)), sync = device [2] zeroed
+cudaError_t launch_train_tc64(const TrainStepArgs &t, uint32_t steps, const float *c12, unsigned int *sync,
+                              cudaStream_t s);
 uint32_t *train_err_word();
 // forward / backward / loss-grad for explicit arrays (nnsort_mlp_* entry points)
 cudaError_t launch_mlp_forward(const PadArch &a, const float *params, const float *x, uint64_t n,

@@ -520,8 +520,8 @@ template <int H1, int H2> static size_t grad_smem() {
 }
 
 int train_grad_blocks(const PadArch &a, uint64_t nsamples) {
-    // width 64: the tensor-core kernel, two partial rows per block
-    if (a.layers == 2 && a.h1 == 64) return 2 * grad_tc64_blocks(nsamples);
+    // width 64: the tensor-core kernel
+    if (a.layers == 2 && a.h1 == 64) return grad_tc64_blocks(nsamples);
     // the block-product kernel (two hidden layers of 32) takes four chunks per block, so its
     // thousands of per-block partial gradients stay few; the per-sample kernel of the small shapes
     // takes one chunk per block, so small batches still spread over the GPU; at most 1024 blocks
@@ -583,38 +583,48 @@ struct ReduceArgs {
     float lr, b1, b2, eps, c1, c2;
 };
 
-// one warp per parameter (the last warp also sums the loss): lane l adds partials l, l + 32, ...
-// in order, loading eight at a time, then the lanes' sums meet in a fixed shuffle tree, so the
-// result does not depend on timing
-__device__ __forceinline__ float warp_fixed_sum(const float *v, size_t stride, int n) {
-    const int lane = threadIdx.x & 31;
+// A block takes 32 parameters (lane l: parameter 32 b + l) and its warp w adds partial rows w, w + 16,
+// ... in order, issuing eight row loads before the first add (each load one coalesced 128-byte row
+// segment); the sixteen warp sums then meet in warp order. One more block sums the loss partials
+// the same way. The result does not depend on timing.
+constexpr int RD_WARPS = 16;
+__device__ __forceinline__ float rows_sum(const float *col, size_t stride, int rows, int w, bool active) {
     float acc = 0.0f;
-    for (int b0 = lane; b0 < n; b0 += 32 * 8) {
+    for (int b0 = w; b0 < rows; b0 += RD_WARPS * 8) {
         float t[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int b = b0 + 32 * q;
-            t[q] = b < n ? v[(size_t)b * stride] : 0.0f;
+            const int b = b0 + RD_WARPS * q;
+            t[q] = (active && b < rows) ? col[(size_t)b * stride] : 0.0f;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            if (b0 + 32 * q < n) acc = __fadd_rn(acc, t[q]);
+            if (b0 + RD_WARPS * q < rows) acc = __fadd_rn(acc, t[q]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_down_sync(0xFFFFFFFFu, acc, o));
     return acc;
 }
 
-__global__ void k_reduce(ReduceArgs r) {
-    const size_t p = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (p == r.P && r.loss_partials && r.loss_out) {
-        const float l = warp_fixed_sum(r.loss_partials, 1, r.blocks);
-        if (lane == 0) *r.loss_out = l * r.loss_scale;
+__global__ void __launch_bounds__(RD_WARPS * 32) k_reduce(ReduceArgs r) {
+    __shared__ float sh[RD_WARPS][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t nb = (r.P + 31) / 32;
+    if (blockIdx.x == nb) {  // the loss
+        const bool on = r.loss_partials && r.loss_out && lane == 0;
+        sh[w][lane] = rows_sum(r.loss_partials, 1, r.blocks, w, on);
+        __syncthreads();
+        if (on && w == 0) {
+            float l = 0.0f;
+            for (int q = 0; q < RD_WARPS; ++q) l = __fadd_rn(l, sh[q][0]);
+            *r.loss_out = l * r.loss_scale;
+        }
+        return;
     }
-    if (p >= r.P) return;
-    const float g = warp_fixed_sum(r.partials + p, r.P, r.blocks);
-    if (lane != 0) return;
+    const size_t p = (size_t)blockIdx.x * 32 + lane;
+    sh[w][lane] = rows_sum(r.partials + p, r.P, r.blocks, w, p < r.P);
+    __syncthreads();
+    if (w != 0 || p >= r.P) return;
+    float g = 0.0f;
+    for (int q = 0; q < RD_WARPS; ++q) g = __fadd_rn(g, sh[q][lane]);
     if (r.out) r.out[p] = g;
     if (r.params) {
         const float m = r.b1 * r.m[p] + (1.0f - r.b1) * g;
@@ -627,6 +637,7 @@ __global__ void k_reduce(ReduceArgs r) {
         r.params[p] = np;
     }
 }
+static unsigned reduce_grid(size_t P) { return (unsigned)((P + 31) / 32 + 1); }
 
 cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, float *out,
                                    const float *loss_partials, float *loss_out, float scale,
@@ -634,7 +645,7 @@ cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, 
     ReduceArgs r{};
     r.partials = partials; r.blocks = blocks; r.P = P; r.out = out;
     r.loss_partials = loss_partials; r.loss_out = loss_out; r.loss_scale = scale;
-    k_reduce<<<(unsigned)(((P + 1) * 32 + 255) / 256), 256, 0, s>>>(r);
+    k_reduce<<<reduce_grid(P), RD_WARPS * 32, 0, s>>>(r);
     return nns_launched(cudaGetLastError());
 }
 
@@ -656,7 +667,7 @@ cudaError_t launch_train_step(const PadArch &a, const TrainStepArgs &t, cudaStre
     const double c1 = 1.0 - std::pow((double)t.b1, (double)(t.step + 1));
     const double c2 = 1.0 - std::pow((double)t.b2, (double)(t.step + 1));
     r.c1 = (float)c1; r.c2 = (float)c2;
-    k_reduce<<<(unsigned)(((t.P + 1) * 32 + 255) / 256), 256, 0, s>>>(r);
+    k_reduce<<<reduce_grid(t.P), RD_WARPS * 32, 0, s>>>(r);
     return nns_launched(cudaGetLastError());
 }
 
