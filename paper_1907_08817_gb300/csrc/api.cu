@@ -1494,7 +1494,7 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
     float *dmask = dg + Pp;
     float *dpart = dmask + Pp, *dlp = dpart + (size_t)blocks * Pp, *dloss = dlp + blocks;
     float *dc12 = dloss + nst;                                           // [2 * steps]
-    unsigned int *dsync = reinterpret_cast<unsigned int *>(dc12 + 2 * (size_t)nst);  // [2]
+    unsigned int *dcount = reinterpret_cast<unsigned int *>(dc12 + 2 * (size_t)nst);  // [1]
     nnsort_model_desc d;
     int rc = nnsort_sample_labels(d_keys, n, dtype, S, o.seed, o.translate, &d, dx, dlab, nullptr, s);
     if (rc) { cudaFreeAsync(dx, s); return rc; }
@@ -1540,8 +1540,8 @@ int nnsort_train(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_tra
             c12[o.steps + k] = (float)(1.0 - std::pow((double)o.beta2, (double)(k + 1)));
         }
         CK(cudaMemcpyAsync(dc12, c12.data(), c12.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(dsync, 0, 2 * sizeof(unsigned int), s));
-        CK(launch_train_tc64(t, o.steps, dc12, dsync, s));
+        CK(cudaMemsetAsync(dcount, 0, sizeof(unsigned int), s));
+        CK(launch_train_tc64(t, o.steps, dc12, dcount, s));
     } else {
         for (uint32_t k = 0; k < o.steps; ++k) {
             t.step = (int)k;

@@ -269,8 +269,9 @@ int train_grad_blocks(const PadArch &a, uint64_t nsamples);
 int grad_tc64_blocks(uint64_t nsamples);
 cudaError_t launch_grad_tc64(const GradArgs &g, cudaStream_t s);
 // every Adam step of a training run of that model in one cooperative launch: c12 = device
-// [2 * steps] bias corrections (1 - beta1^(t+1), then 1 - beta2^(t+1)), sync = device [2] zeroed
-cudaError_t launch_train_tc64(const TrainStepArgs &t, uint32_t steps, const float *c12, unsigned int *sync,
+// [2 * steps] bias corrections (1 - beta1^(t+1), then 1 - beta2^(t+1)), count = a device word zeroed
+// before the launch
+cudaError_t launch_train_tc64(const TrainStepArgs &t, uint32_t steps, const float *c12, unsigned int *count,
                               cudaStream_t s);
 uint32_t *train_err_word();
 // forward / backward / loss-grad for explicit arrays (nnsort_mlp_* entry points)

@@ -76,6 +76,9 @@ constexpr uint32_t I_VEC = idesc_bf16(GM, 16, true, true);
 
 __device__ __forceinline__ uint64_t kdesc(uint32_t addr, uint32_t ch) { return mdesc(addr, ch, 128); }
 __device__ __forceinline__ uint64_t mndesc(uint32_t addr, uint32_t ch) { return mdesc(addr, 128, ch); }
+// the descriptor of the matrix `bytes` further on: the start-address field (address / 16, bits 0-13)
+// of a base below 256 KB does not carry into the next field
+__device__ __forceinline__ uint64_t at(uint64_t desc, uint32_t bytes) { return desc + (uint64_t)(bytes >> 4); }
 
 // two binary32 values as BF16 (first in the low half), rounded to nearest
 __device__ __forceinline__ uint32_t bf2_rn(float first, float second) {
@@ -159,6 +162,24 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
     // thread (sample s, half hf): warps 0-3 of the group take units 0-31, warps 4-7 units 32-63;
     // warp w reads tensor-memory lanes 32 (w % 4) ..
     const int wq = (gt >> 5) & 3, hf = gt >> 7, s = wq * 32 + (gt & 31), u0 = hf * GU;
+    const uint64_t nchunks = (g.n + GM - 1) / GM;
+    const uint64_t ngroups = (uint64_t)gridDim.x * GNG;
+    // this thread's sample inputs, loaded one chunk ahead (the first while the
+    // parameters are staged)
+    auto load_inputs = [&](uint64_t c, float &x, float &lab, float &gyin) {
+        const uint64_t i = c * GM + s;
+        x = 0.0f; lab = 0.0f; gyin = 0.0f;
+        if (c < nchunks && i < g.n) {
+            uint64_t src = i;
+            if (g.mode == 2) src = __umul64hi(rng_draw(g.bseed, g.bofs + i), g.S);
+            x = g.x[src];
+            if (g.mode != 0) lab = g.label[src];
+            else gyin = g.gy[i];
+        }
+    };
+    uint64_t c = (uint64_t)blockIdx.x * GNG + grp;
+    float nx, nlab, ngy;
+    load_inputs(c, nx, nlab, ngy);
     {   // W2 as three BF16 parts; the vectors in binary32; the zero columns 8..15 of V
         const float *P = g.params;
         for (int e = tid; e < GH * GH; e += GTHREADS) {
@@ -197,26 +218,11 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
     const int bid = 1 + grp;
     const bool issuer = gt == 0;
     const float b3 = par[4 * GH];
-    const uint64_t nchunks = (g.n + GM - 1) / GM;
-    const uint64_t ngroups = (uint64_t)gridDim.x * GNG;
+    // descriptor bases: activations K-major (KA) and MN-major (MA), W2 K-major (KW) and MN-major (MW)
+    const uint64_t KA = kdesc(rb, CH_ACT), MA = mndesc(rb, CH_ACT), KW = kdesc(wb, CH_W), MW = mndesc(wb, CH_W);
     uint32_t phase = pp.phase, phase2 = pp.phase2, err = pp.err, last_bar = pp.last_bar, last_par = pp.last_par;
     bool dead = pp.dead, first = true;
     float pgy = 0.0f, plv = 0.0f;
-    // this thread's sample inputs, loaded one chunk ahead
-    auto load_inputs = [&](uint64_t c, float &x, float &lab, float &gyin) {
-        const uint64_t i = c * GM + s;
-        x = 0.0f; lab = 0.0f; gyin = 0.0f;
-        if (c < nchunks && i < g.n) {
-            uint64_t src = i;
-            if (g.mode == 2) src = __umul64hi(rng_draw(g.bseed, g.bofs + i), g.S);
-            x = g.x[src];
-            if (g.mode != 0) lab = g.label[src];
-            else gyin = g.gy[i];
-        }
-    };
-    uint64_t c = (uint64_t)blockIdx.x * GNG + grp;
-    float nx, nlab, ngy;
-    load_inputs(c, nx, nlab, ngy);
     for (; c < nchunks; c += ngroups) {
         const uint64_t i = c * GM + s;
         const bool valid = i < g.n;
@@ -253,14 +259,14 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
 
         // 2. Z = H1 W2^T (this commit also covers the previous chunk's column sums)
         if (issuer && !dead) {
-            const uint32_t ha[3] = {rb + O_H1, rb + O_H1 + PART, rb + O_R1};
-            const int pa[6] = {2, 0, 1, 1, 0, 0}, pb[6] = {0, 2, 1, 0, 1, 0};
+            constexpr uint32_t ha[3] = {O_H1, O_H1 + PART, O_R1};
+            constexpr int pa[6] = {2, 0, 1, 1, 0, 0}, pb[6] = {0, 2, 1, 0, 1, 0};
 #pragma unroll
             for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
                 for (int ks = 0; ks < GH / 16; ++ks)
-                    mma_bf16(tb + C_Z, kdesc(ha[pa[pr]] + ks * 2 * CH_ACT, CH_ACT),
-                             kdesc(wb + pb[pr] * WPART + ks * 2 * CH_W, CH_W), I_ZK, (pr | ks) ? 1u : 0u);
+                    mma_bf16(tb + C_Z, at(KA, ha[pa[pr]] + ks * 2 * CH_ACT), at(KW, pb[pr] * WPART + ks * 2 * CH_W),
+                             I_ZK, (pr | ks) ? 1u : 0u);
             mma_commit(mybar);
             last_bar = mybar;
             last_par = phase;
@@ -362,24 +368,22 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
         if (issuer && !dead) {
 #pragma unroll
             for (int ks = 0; ks < GM / 16; ++ks)
-                mma_bf16(tb + C_W3, mndesc(rb + O_R3 + ks * 256, CH_ACT), mndesc(rb + O_V + ks * 256, CH_ACT),
-                         I_VEC, (!first || ks) ? 1u : 0u);
+                mma_bf16(tb + C_W3, at(MA, O_R3 + ks * 256), at(MA, O_V + ks * 256), I_VEC, (!first || ks) ? 1u : 0u);
             // the three part products of weight >= 2^-8 (the rest is below 2^-16 of D1pre)
-            const uint32_t da[2] = {rb + O_R1, rb + O_R1 + PART};
-            const int qa[3] = {1, 0, 0}, qb[3] = {0, 1, 0};
+            constexpr int qa[3] = {1, 0, 0}, qb[3] = {0, 1, 0};
 #pragma unroll
             for (int pr = 0; pr < 3; ++pr)
 #pragma unroll
                 for (int ks = 0; ks < GH / 16; ++ks)
-                    mma_bf16(tb + C_Z, kdesc(da[qa[pr]] + ks * 2 * CH_ACT, CH_ACT),
-                             mndesc(wb + qb[pr] * WPART + ks * 256, CH_W), I_D1, (pr | ks) ? 1u : 0u);
+                    mma_bf16(tb + C_Z, at(KA, O_R1 + qa[pr] * PART + ks * 2 * CH_ACT), at(MW, qb[pr] * WPART + ks * 256),
+                             I_D1, (pr | ks) ? 1u : 0u);
             mma_commit(mybar);
 #pragma unroll
             for (int ks = 0; ks < GM / 16; ++ks) {
                 const uint32_t acc = (!first || ks) ? 1u : 0u;
-                const uint64_t d2 = mndesc(rb + O_R1 + ks * 256, CH_ACT);
-                mma_bf16(tb + C_W2, d2, mndesc(rb + O_H1 + ks * 256, CH_ACT), I_W2, acc);
-                mma_bf16(tb + C_B2, d2, mndesc(rb + O_V + ks * 256, CH_ACT), I_VEC, acc);
+                const uint64_t d2 = at(MA, O_R1 + ks * 256);
+                mma_bf16(tb + C_W2, d2, at(MA, O_H1 + ks * 256), I_W2, acc);
+                mma_bf16(tb + C_B2, d2, at(MA, O_V + ks * 256), I_VEC, acc);
             }
             mma_commit(mybar2);
             last_bar = mybar2;
@@ -449,8 +453,7 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
         if (issuer && !dead) {
 #pragma unroll
             for (int ks = 0; ks < GM / 16; ++ks)
-                mma_bf16(tb + C_V1, mndesc(rb + O_R3 + ks * 256, CH_ACT), mndesc(rb + O_V + ks * 256, CH_ACT),
-                         I_VEC, (!first || ks) ? 1u : 0u);
+                mma_bf16(tb + C_V1, at(MA, O_R3 + ks * 256), at(MA, O_V + ks * 256), I_VEC, (!first || ks) ? 1u : 0u);
         }
         first = false;
     }
@@ -582,9 +585,10 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_grad_tc64(GradArgs g) {
 }
 
 // ---- every Adam step of a training run in one cooperative launch
-// Per step: the gradient pass (partial rows), a grid-wide meeting, the fixed-order sum of the rows
-// and the Adam update of this block's parameter groups (32 parameters each, groups assigned
-// round-robin), another meeting, so the next pass reads the updated parameters.
+// Per step: the gradient pass (one partial row per block), a grid-wide meeting, the fixed-order sum
+// of the rows and the Adam update of this block's parameter groups (32 parameters each, groups
+// assigned round-robin; the owner of group 0 also sums the loss), another meeting, so the next pass
+// reads the updated parameters.
 struct TrainTcArgs {
     GradArgs g;                // n = batch; bofs of step t = t * n
     float *params;             // = g.params, updated in place
@@ -594,41 +598,35 @@ struct TrainTcArgs {
     float *loss_out;           // [steps]
     float loss_scale, lr, b1, b2, eps;
     int steps;
-    unsigned int *sync;        // [2]: arrivals, generation; zero before the launch
+    unsigned int *count;       // arrivals at the grid meetings (zero before the launch)
 };
+constexpr int NGRP = (GP + 31) / 32;  // parameter groups
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-
-// all blocks of the launch meet (co-resident by the cooperative launch); false when the wait gave
-// up after the library's spin limit
-__device__ __forceinline__ bool grid_meet(unsigned int *sync, unsigned int &gen) {
+// All blocks of the launch meet (they are co-resident: cooperative launch). The arrival count only
+// grows: meeting k is complete when it reaches k * gridDim.x. The block's earlier global writes are
+// released with the arrival (after the block barrier) and acquired by every block that sees the
+// count complete. False when the wait gave up after the library's spin limit.
+__device__ __forceinline__ bool grid_meet(unsigned int *count, unsigned int &target) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned int target = gen + 1;
-        __threadfence();
-        if (atomicAdd(&sync[0], 1u) == gridDim.x - 1) {
-            atomicExch(&sync[0], 0u);
-            __threadfence();
-            atomicExch(&sync[1], target);
-        } else {
-            const unsigned long long t0 = globaltimer_ns();
-            uint32_t polls = 0;
-            while (ld_acquire_u32(&sync[1]) != target) {
-                if (globaltimer_ns() - t0 > SPIN_LIMIT_NS || ++polls > SPIN_LIMIT_POLLS) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        target += gridDim.x;
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+        const unsigned long long t0 = globaltimer_ns();
+        uint32_t polls = 0;
+        while (ld_acquire_u32(count) < target) {
+            if (globaltimer_ns() - t0 > SPIN_LIMIT_NS || ++polls > SPIN_LIMIT_POLLS) {
+                ok = 0;
+                break;
             }
+            __nanosleep(64);
         }
-        __threadfence();
-        gen = target;
         ok_s = ok;
     }
     __syncthreads();
@@ -637,11 +635,12 @@ __device__ __forceinline__ bool grid_meet(unsigned int *sync, unsigned int &gen)
 
 constexpr int RW = GTHREADS / 32;  // warps of the reduction
 
+// the fixed-order sum of the partial rows and Adam, for this block's parameter groups
 __device__ __forceinline__ void reduce_adam(const TrainTcArgs &a, int step, float (*red)[33]) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nb = gridDim.x, ngrp = (GP + 31) / 32;
+    const int nb = gridDim.x;
     const float c1 = a.c12[step], c2 = a.c12[a.steps + step];
-    for (int pg = blockIdx.x; pg < ngrp; pg += nb) {
+    for (int pg = blockIdx.x; pg < NGRP; pg += nb) {
         const int p = pg * 32 + lane;
         float acc = 0.0f;
         for (int r0 = w; r0 < nb; r0 += RW * 8) {
@@ -669,20 +668,20 @@ __device__ __forceinline__ void reduce_adam(const TrainTcArgs &a, int step, floa
             if (a.mask && a.mask[p] * np < 0.0f) np = 0.0f;  // monotone projection
             a.params[p] = np;
         }
-        __syncthreads();
-    }
-    if (blockIdx.x == nb - 1 && a.loss_out) {
-        float acc = 0.0f;
-        if (lane == 0)
-            for (int r = w; r < nb; r += RW) acc = __fadd_rn(acc, __ldcg(a.g.loss_partials + r));
-        red[w][0] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (pg == 0 && a.loss_out) {  // the loss
+            __syncthreads();
             float l = 0.0f;
-            for (int q = 0; q < RW; ++q) l = __fadd_rn(l, red[q][0]);
-            a.loss_out[step] = l * a.loss_scale;
+            if (lane == 0)
+                for (int r = w; r < nb; r += RW) l = __fadd_rn(l, __ldcg(a.g.loss_partials + r));
+            red[w][0] = l;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float sum = 0.0f;
+                for (int q = 0; q < RW; ++q) sum = __fadd_rn(sum, red[q][0]);
+                a.loss_out[step] = sum * a.loss_scale;
+            }
         }
-        __syncthreads();
+        __syncthreads();  // red is rewritten by the next group
     }
 }
 
@@ -694,17 +693,17 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_train_tc64(TrainTcArgs a) {
     float(*red)[33] = reinterpret_cast<float(*)[33]>(sm + OFF_GRP);
     Pipe pp;
     pipe_open(pp, &tmem_slot, bars);
-    unsigned int gen = 0;
+    unsigned int target = 0;
     for (int step = 0; step < a.steps; ++step) {
         GradArgs g = a.g;
         g.bofs = (uint64_t)step * g.n;
         grad_pass(g, sm, pp, g.partials + (size_t)blockIdx.x * GP, g.loss_partials + blockIdx.x);
-        if (!grid_meet(a.sync, gen)) {
+        if (!grid_meet(a.count, target)) {
             pp.err |= ERR_TIMEOUT;
             break;
         }
         reduce_adam(a, step, red);
-        if (!grid_meet(a.sync, gen)) {
+        if (!grid_meet(a.count, target)) {
             pp.err |= ERR_TIMEOUT;
             break;
         }
@@ -729,7 +728,7 @@ cudaError_t launch_grad_tc64(const GradArgs &g, cudaStream_t s) {
     return e;
 }
 
-cudaError_t launch_train_tc64(const TrainStepArgs &t, uint32_t steps, const float *c12, unsigned int *sync,
+cudaError_t launch_train_tc64(const TrainStepArgs &t, uint32_t steps, const float *c12, unsigned int *count,
                               cudaStream_t s) {
     if (steps == 0) return cudaSuccess;
     const uint64_t B = t.batch ? t.batch : t.S;
@@ -751,7 +750,7 @@ cudaError_t launch_train_tc64(const TrainStepArgs &t, uint32_t steps, const floa
     a.g.loss_partials = t.loss_partials; a.g.gx = nullptr;
     a.params = t.params; a.m = t.m; a.v = t.v; a.mask = t.mask; a.c12 = c12; a.loss_out = t.loss_out;
     a.loss_scale = 1.0f / (float)B; a.lr = t.lr; a.b1 = t.b1; a.b2 = t.b2; a.eps = t.eps;
-    a.steps = (int)steps; a.sync = sync;
+    a.steps = (int)steps; a.count = count;
     void *args[] = {&a};
     e = cudaLaunchCooperativeKernel((const void *)k_train_tc64, dim3((unsigned)blocks), dim3(GTHREADS), args,
                                     SMEM_BYTES, s);
