@@ -216,7 +216,8 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
     const uint32_t rb = smem_u32(R), wb = smem_u32(sm + OFF_W);
     const uint32_t mybar = pp.bar, mybar2 = pp.bar2;
     const int bid = 1 + grp;
-    const bool issuer = gt == 0;
+    // warp 0 of the group issues the MMAs (one elected lane) and waits for them
+    const bool issuer = (gt >> 5) == 0;
     const float b3 = par[4 * GH];
     // descriptor bases: activations K-major (KA) and MN-major (MA), W2 K-major (KW) and MN-major (MW)
     const uint64_t KA = kdesc(rb, CH_ACT), MA = mndesc(rb, CH_ACT), KW = kdesc(wb, CH_W), MW = mndesc(wb, CH_W);
@@ -265,12 +266,12 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
             for (int pr = 0; pr < 6; ++pr)
 #pragma unroll
                 for (int ks = 0; ks < GH / 16; ++ks)
-                    mma_bf16(tb + C_Z, at(KA, ha[pa[pr]] + ks * 2 * CH_ACT), at(KW, pb[pr] * WPART + ks * 2 * CH_W),
+                    mma_bf16_warp(tb + C_Z, at(KA, ha[pa[pr]] + ks * 2 * CH_ACT), at(KW, pb[pr] * WPART + ks * 2 * CH_W),
                              I_ZK, (pr | ks) ? 1u : 0u);
-            mma_commit(mybar);
+            mma_commit_warp(mybar);
             last_bar = mybar;
             last_par = phase;
-            if (!mbar_wait(mybar, phase)) {
+            if (__any_sync(0xFFFFFFFFu, !mbar_wait(mybar, phase))) {
                 dead = true;
                 err |= ERR_TIMEOUT;
             }
@@ -368,27 +369,27 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
         if (issuer && !dead) {
 #pragma unroll
             for (int ks = 0; ks < GM / 16; ++ks)
-                mma_bf16(tb + C_W3, at(MA, O_R3 + ks * 256), at(MA, O_V + ks * 256), I_VEC, (!first || ks) ? 1u : 0u);
+                mma_bf16_warp(tb + C_W3, at(MA, O_R3 + ks * 256), at(MA, O_V + ks * 256), I_VEC, (!first || ks) ? 1u : 0u);
             // the three part products of weight >= 2^-8 (the rest is below 2^-16 of D1pre)
             constexpr int qa[3] = {1, 0, 0}, qb[3] = {0, 1, 0};
 #pragma unroll
             for (int pr = 0; pr < 3; ++pr)
 #pragma unroll
                 for (int ks = 0; ks < GH / 16; ++ks)
-                    mma_bf16(tb + C_Z, at(KA, O_R1 + qa[pr] * PART + ks * 2 * CH_ACT), at(MW, qb[pr] * WPART + ks * 256),
+                    mma_bf16_warp(tb + C_Z, at(KA, O_R1 + qa[pr] * PART + ks * 2 * CH_ACT), at(MW, qb[pr] * WPART + ks * 256),
                              I_D1, (pr | ks) ? 1u : 0u);
-            mma_commit(mybar);
+            mma_commit_warp(mybar);
 #pragma unroll
             for (int ks = 0; ks < GM / 16; ++ks) {
                 const uint32_t acc = (!first || ks) ? 1u : 0u;
                 const uint64_t d2 = at(MA, O_R1 + ks * 256);
-                mma_bf16(tb + C_W2, d2, at(MA, O_H1 + ks * 256), I_W2, acc);
-                mma_bf16(tb + C_B2, d2, at(MA, O_V + ks * 256), I_VEC, acc);
+                mma_bf16_warp(tb + C_W2, d2, at(MA, O_H1 + ks * 256), I_W2, acc);
+                mma_bf16_warp(tb + C_B2, d2, at(MA, O_V + ks * 256), I_VEC, acc);
             }
-            mma_commit(mybar2);
+            mma_commit_warp(mybar2);
             last_bar = mybar2;
             last_par = phase2;
-            if (!mbar_wait(mybar, phase)) {
+            if (__any_sync(0xFFFFFFFFu, !mbar_wait(mybar, phase))) {
                 dead = true;
                 err |= ERR_TIMEOUT;
             }
@@ -440,7 +441,7 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
         fence_async_smem();
         // the next chunk's H1 rows overwrite what dW2 += D2^T H1 reads
         if (issuer && !dead) {
-            if (!mbar_wait(mybar2, phase2)) {
+            if (__any_sync(0xFFFFFFFFu, !mbar_wait(mybar2, phase2))) {
                 dead = true;
                 err |= ERR_TIMEOUT;
             }
@@ -453,15 +454,15 @@ __device__ __forceinline__ void grad_pass(const GradArgs &g, unsigned char *sm, 
         if (issuer && !dead) {
 #pragma unroll
             for (int ks = 0; ks < GM / 16; ++ks)
-                mma_bf16(tb + C_V1, at(MA, O_R3 + ks * 256), at(MA, O_V + ks * 256), I_VEC, (!first || ks) ? 1u : 0u);
+                mma_bf16_warp(tb + C_V1, at(MA, O_R3 + ks * 256), at(MA, O_V + ks * 256), I_VEC, (!first || ks) ? 1u : 0u);
         }
         first = false;
     }
     if (issuer && !dead && !first) {
-        mma_commit(mybar);
+        mma_commit_warp(mybar);
         last_bar = mybar;
         last_par = phase;
-        if (!mbar_wait(mybar, phase)) {
+        if (__any_sync(0xFFFFFFFFu, !mbar_wait(mybar, phase))) {
             dead = true;
             err |= ERR_TIMEOUT;
         }
@@ -565,7 +566,7 @@ __device__ __forceinline__ void pipe_close(Pipe &pp) {
     if (pp.err) atomicOr(&g_train_err, pp.err);
     // an MMA whose completion was not seen may still be running: wait for it (bounded) before the
     // tensor memory it writes is released
-    if (pp.dead && (threadIdx.x % GT) == 0) mbar_wait(pp.last_bar, pp.last_par);
+    if (pp.dead && (threadIdx.x % GT) < 32) mbar_wait(pp.last_bar, pp.last_par);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
