@@ -341,7 +341,8 @@ int nnsort_model_create(const nnsort_model_desc *desc, const float *h_params, nn
     f->params.assign(h_params, h_params + f->P);
     f->pad = pad_arch(desc->layers, desc->h1, desc->h2);
     f->Ppad = padded_param_count(f->pad);
-    const std::vector<float> pp = to_padded(*desc, f->pad, h_params);
+    f->hpad = to_padded(*desc, f->pad, h_params);
+    const std::vector<float> &pp = f->hpad;
     cudaGetDevice(&f->device);
     cudaError_t e = cudaMalloc(&f->d_params, f->Ppad * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(f->d_params, pp.data(), f->Ppad * sizeof(float), cudaMemcpyHostToDevice);
@@ -831,6 +832,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     pa.dtype = dtype;
     pa.pwl = pwl_dev;
     pa.single_model = (single && f0 && !o.d_slots) ? 1 : 0;
+    pa.host_pad = f0 ? f0->hpad.data() : nullptr;
     const PadArch arch = f0 ? f0->pad : pad_arch(1, 8, 0);
     const int prec = f0 ? o.precision : NNSORT_PREC_FP32;
     {
@@ -1203,6 +1205,7 @@ int nnsort_predict(const void *d_keys, uint64_t n, int32_t dtype, const nnsort_m
     pa.dtype = dtype;
     pa.pwl = pwl_dev;
     pa.single_model = 1;
+    pa.host_pad = f->hpad.data();
     w->last_err = err;
     cudaError_t e = launch_predict(f->pad, precision, pa, sm_count(), stream);
     if (e == cudaErrorNotSupported) return NNSORT_E_UNSUPPORTED;
@@ -1464,6 +1467,7 @@ int nnsort_train_batch(void *const *d_keys, const uint64_t *ns, int32_t count, i
         f->params = up;
         f->pad = pa;
         f->Ppad = Pp;
+        f->hpad.assign(pp, pp + Pp);
         f->d_params = dpar + (size_t)j * Pp;
         f->owner = block;
         cudaGetDevice(&f->device);

@@ -67,6 +67,7 @@ struct PredictArgs {
     int dtype;
     PwlDev pwl;              // NNSORT_PREC_PWL (single array)
     int single_model;        // 1: one array whose positions come from its model (no injected slots)
+    const float *host_pad;   // single_model: that model's padded parameters in host memory
 };
 cudaError_t launch_predict(const PadArch &a, int precision, const PredictArgs &p, int sms,
                            cudaStream_t s);
@@ -292,6 +293,8 @@ cudaError_t launch_reduce_partials(const float *partials, int blocks, size_t P, 
 struct nnsort_model {
     nnsort_model_desc desc;
     std::vector<float> params;  // caller layout
+    std::vector<float> hpad;    // padded layout in host memory (the tensor-core predict passes its
+                                // vectors as launch constants)
     nns::PadArch pad;
     size_t P = 0, Ppad = 0;
     float *d_params = nullptr;  // padded layout

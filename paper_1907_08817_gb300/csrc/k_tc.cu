@@ -365,6 +365,12 @@ __device__ __forceinline__ bool grp_or(int id, bool v) {
     return r != 0;
 }
 
+// the first and last layers' parameters as launch constants: every thread reads them through the
+// constant cache (one broadcast per warp instruction, no shared-memory traffic)
+struct TcConst {
+    float w1[64], b1[64], w3[64], b3;
+};
+
 template <int H, bool SPLIT, int NG>
 __host__ __device__ constexpr size_t tcmg_smem_bytes() {
     return (size_t)NG * (SPLIT ? 2 : 1) * TC_M * H * 2 + (size_t)(SPLIT ? 2 : 1) * H * H * 2 +
@@ -372,7 +378,7 @@ __host__ __device__ constexpr size_t tcmg_smem_bytes() {
 }
 
 template <int H, typename W, bool SPLIT, int NG>
-__global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictArgs a) {
+__global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictArgs a, const TcConst cst) {
     static_assert(H == 16 || H == 32 || H == 64, "tensor path widths");
     static_assert(NG * H <= 512, "accumulators fit in tensor memory");
     constexpr int NT = SPLIT ? 2 : 1;
@@ -385,8 +391,6 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
     unsigned char *sB16 = sB + H * H * 2;
     unsigned char *sOnes = sB + NT * H * H * 2;                       // TC_M x 16 bf16
     unsigned char *sBias = sOnes + TC_M * 16 * 2;                     // H x 16 bf16
-    float *pf = reinterpret_cast<float *>(sBias + H * 16 * 2);      // W1 | b1 | b2 | W3 | b3
-    const float4 *pv = reinterpret_cast<const float4 *>(pf);
     __shared__ __align__(8) unsigned long long bar[NG];
     __shared__ uint32_t tmem_base;
 
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     const Seg &sg = a.segs[0];
-    {   // W2 (row = output unit, K = input unit) -> canonical K-major layout; parameters
+    {   // W2 (row = output unit, K = input unit) -> canonical K-major layout; bias slabs
         const float *W2 = sg.params + 2 * H;
         for (int e = tid; e < H * H; e += NG * TC_THREADS) {
             const int nrow = e / H, k = e % H;
@@ -406,13 +410,6 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
             *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16_rn(W2[e]);
             if (SPLIT) *reinterpret_cast<__half *>(sB16 + off) = __float2half_rn(W2[e]);
         }
-        for (int e = tid; e < H; e += NG * TC_THREADS) {
-            pf[e] = sg.params[e];
-            pf[H + e] = sg.params[H + e];
-            pf[2 * H + e] = sg.params[2 * H + H * H + e];
-            pf[3 * H + e] = sg.params[3 * H + H * H + e];
-        }
-        if (tid == 0) pf[4 * H] = sg.params[4 * H + H * H];
         fill_bias_slabs<H>(sOnes, sBias, sg.params + 2 * H + H * H, tid, NG * TC_THREADS);
     }
     fence_async_smem();
@@ -452,15 +449,12 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
         const unsigned long long xx = pk2(x, x);
 #pragma unroll
         for (int j0 = 0; j0 < H; j0 += 8) {
-            const float4 wa = pv[j0 / 4], wb = pv[j0 / 4 + 1];
-            const float4 ba = pv[H / 4 + j0 / 4], bb = pv[H / 4 + j0 / 4 + 1];
-            const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-            const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                const int j = j0 + 2 * q;
                 const unsigned long long hh =
-                    fma2_rn(pk2(w8[2 * q], w8[2 * q + 1]), xx, pk2(b8[2 * q], b8[2 * q + 1]));
+                    fma2_rn(pk2(cst.w1[j], cst.w1[j + 1]), xx, pk2(cst.b1[j], cst.b1[j + 1]));
                 float h0, h1;
                 upk2(hh, h0, h1);
                 if (!SPLIT) {
@@ -508,7 +502,7 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
         phase ^= 1u;
         dead = grp_or(bid, dead);
         tc_fence_after();
-        unsigned long long yy = pk2(pf[4 * H], 0.0f);
+        unsigned long long yy = pk2(cst.b3, 0.0f);
 #pragma unroll
         for (int c0 = 0; c0 < H; c0 += 16) {
             float acc[16];
@@ -520,11 +514,8 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
                 for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
             }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float4 wq = pv[3 * H / 4 + c0 / 4 + v];
-                yy = fma2_rn(pk2(wq.x, wq.y), pk2(relu_f(acc[4 * v]), relu_f(acc[4 * v + 1])), yy);
-                yy = fma2_rn(pk2(wq.z, wq.w), pk2(relu_f(acc[4 * v + 2]), relu_f(acc[4 * v + 3])), yy);
-            }
+            for (int q = 0; q < 16; q += 2)
+                yy = fma2_rn(pk2(cst.w3[c0 + q], cst.w3[c0 + q + 1]), pk2(relu_f(acc[q]), relu_f(acc[q + 1])), yy);
         }
         tc_fence_before();
         if (!valid) continue;
@@ -553,6 +544,14 @@ __global__ void __launch_bounds__(NG * TC_THREADS, 1) k_predict_bf16_mg(PredictA
 
 template <int H, bool SPLIT>
 static cudaError_t bf16_mg_go(const PredictArgs &p, int sms, cudaStream_t s) {
+    // padded layout: W1[H] b1[H] W2[H * H] b2[H] W3[H] b3
+    TcConst c{};
+    for (int j = 0; j < H; ++j) {
+        c.w1[j] = p.host_pad[j];
+        c.b1[j] = p.host_pad[H + j];
+        c.w3[j] = p.host_pad[3 * H + H * H + j];
+    }
+    c.b3 = p.host_pad[4 * H + H * H];
     const uint64_t n_sub = (uint64_t)p.total_tiles * (PRED_TILE / TC_M);
     const size_t smem = tcmg_smem_bytes<H, SPLIT, TC_NG>();
     const int grid = (int)std::min<uint64_t>((n_sub + TC_NG - 1) / TC_NG, (uint64_t)sms);
@@ -562,8 +561,8 @@ static cudaError_t bf16_mg_go(const PredictArgs &p, int sms, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(p.key_bytes == 4 ? k4 : k8,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (p.key_bytes == 4) k4<<<grid, TC_NG * TC_THREADS, smem, s>>>(p);
-    else k8<<<grid, TC_NG * TC_THREADS, smem, s>>>(p);
+    if (p.key_bytes == 4) k4<<<grid, TC_NG * TC_THREADS, smem, s>>>(p, c);
+    else k8<<<grid, TC_NG * TC_THREADS, smem, s>>>(p, c);
     return nns_launched(cudaGetLastError());
 }
 
@@ -599,7 +598,7 @@ constexpr int TC_KPT = 2, TC_KPT_SPLIT = 1;
 
 cudaError_t launch_predict_bf16(const PadArch &a, const PredictArgs &p, bool split, int sms, cudaStream_t s) {
     if (a.layers != 2) return cudaErrorNotSupported;
-    if (p.nseg == 1 && p.single_model) {
+    if (p.nseg == 1 && p.single_model && p.host_pad) {
         switch (a.h1) {
         case 16: return split ? bf16_mg_go<16, true>(p, sms, s) : bf16_mg_go<16, false>(p, sms, s);
         case 32: return split ? bf16_mg_go<32, true>(p, sms, s) : bf16_mg_go<32, false>(p, sms, s);

@@ -188,6 +188,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     pa.key_bytes = kb;
     pa.dtype = dtype;
     pa.single_model = 1;  // one array whose positions come from its model, as in nnsort_sort
+    pa.host_pad = f->hpad.data();
     int sms = 1;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     {
