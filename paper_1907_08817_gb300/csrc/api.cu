@@ -885,6 +885,7 @@ int run_sort(const std::vector<SegIn> &in, const nnsort_sort_opts *op, int dtype
     sa.g_flag = L.g_flag;
     sa.g_x = L.g_x;
     sa.g_y = L.g_y;
+    sa.N = P.N;
     sa.fate = o.d_fate;
     sa.out_rows = L.out_rows;
     sa.key_scratch = L.key[oi];

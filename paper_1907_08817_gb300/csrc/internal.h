@@ -143,6 +143,7 @@ struct SolveArgs {
     // global scratch for buckets beyond on-chip capacity
     uint8_t *g_flag;          // [N]
     uint32_t *g_x, *g_y;  // [N] each
+    uint64_t N;               // elements (the sizes of the [N] scratch arrays)
     int8_t *fate;             // nullable, per row (single array only)
     uint32_t *out_rows;       // [N] rows of the output order (when rows are carried)
     void *key_scratch;        // [N] free partition buffer reused by the seam repair

@@ -403,6 +403,105 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_finalize(SolveArgs a) {
     }
 }
 
+// One large array: k_finalize's scans over tiles of MT_TILE buckets on many blocks, in three
+// launches (tile maxima; their exclusive prefix in one block; each tile's scan from its prefix).
+// Results equal the one-block scan's (the maximum is associative and exact).
+constexpr int MT_THREADS = 256, MT_PER = 4;
+constexpr uint32_t MT_TILE = MT_THREADS * MT_PER;
+
+__device__ __forceinline__ int rounds_of(const Seg &sg, const SegStats &st) {
+    uint32_t t = 0;
+    unsigned long long w = sg.n;
+    while (t < sg.eps && w > sg.tau) {
+        ++t;
+        w = st.count_ge[t];
+    }
+    return (int)t;
+}
+__device__ __forceinline__ KMax kmax_of(const OKey &o) {
+    KMax x; x.k = o.k; x.tb = o.tb; x.valid = o.valid; return x;
+}
+__device__ __forceinline__ OKey okey_of_kmax(const KMax &x) {
+    OKey o; o.k = x.k; o.tb = x.tb; o.valid = x.valid; return o;
+}
+
+// 1) tile maxima per round -> agg[tile * MAXR + r]; block 0 also records t
+__global__ void __launch_bounds__(MT_THREADS) k_finalize_tiles(SolveArgs a, OKey *agg) {
+    __shared__ KMax scratch[33];
+    __shared__ KMax tot;
+    __shared__ int sh_t;
+    const int tid = threadIdx.x;
+    const Seg &sg = a.segs[0];
+    SegStats &st = a.stats[0];
+    if (tid == 0) sh_t = rounds_of(sg, st);
+    __syncthreads();
+    const int t = sh_t;
+    const uint32_t c0 = blockIdx.x * MT_TILE + (uint32_t)tid * MT_PER;
+    for (int r = 0; r < t; ++r) {
+        KMax loc = kmax_none();
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k)
+            if (c0 + k < sg.nb) loc = kmax(loc, kmax_of(a.bmax[(size_t)(sg.bbase + c0 + k) * MAXR + r]));
+        block_excl_max(loc, scratch, &tot);
+        if (tid == 0) agg[(size_t)blockIdx.x * MAXR + r] = okey_of_kmax(tot);
+    }
+}
+// 2) exclusive prefix maxima of the tile maxima (one block; at most MT_THREADS * MT_PER tiles)
+__global__ void __launch_bounds__(MT_THREADS) k_finalize_prefix(SolveArgs a, OKey *agg, uint32_t ntiles) {
+    __shared__ KMax scratch[33];
+    __shared__ int sh_t;
+    const int tid = threadIdx.x;
+    const Seg &sg = a.segs[0];
+    SegStats &st = a.stats[0];
+    if (tid == 0) {
+        const int t = rounds_of(sg, st);
+        st.count_ge[0] = sg.n;
+        st.t = (uint32_t)t;
+        sh_t = t;
+    }
+    __syncthreads();
+    for (int r = 0; r < sh_t; ++r) {
+        KMax v[MT_PER], loc = kmax_none();
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t i = (uint32_t)tid * MT_PER + k;
+            v[k] = i < ntiles ? kmax_of(agg[(size_t)i * MAXR + r]) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = block_excl_max(loc, scratch, nullptr);
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t i = (uint32_t)tid * MT_PER + k;
+            if (i < ntiles) agg[(size_t)i * MAXR + r] = okey_of_kmax(run);
+            run = kmax(run, v[k]);
+        }
+    }
+}
+// 3) each tile's exclusive prefix maxima from the maximum of the tiles before it
+__global__ void __launch_bounds__(MT_THREADS) k_finalize_apply(SolveArgs a, const OKey *agg) {
+    __shared__ KMax scratch[33];
+    __shared__ int sh_t;
+    const int tid = threadIdx.x;
+    const Seg &sg = a.segs[0];
+    if (tid == 0) sh_t = (int)a.stats[0].t;
+    __syncthreads();
+    const uint32_t c0 = blockIdx.x * MT_TILE + (uint32_t)tid * MT_PER;
+    for (int r = 0; r < sh_t; ++r) {
+        KMax v[MT_PER], loc = kmax_none();
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            v[k] = c0 + k < sg.nb ? kmax_of(a.bmax[(size_t)(sg.bbase + c0 + k) * MAXR + r]) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = kmax(kmax_of(agg[(size_t)blockIdx.x * MAXR + r]), block_excl_max(loc, scratch, nullptr));
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            if (c0 + k < sg.nb) a.carry[(size_t)(sg.bbase + c0 + k) * MAXR + r] = okey_of_kmax(run);
+            run = kmax(run, v[k]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // CTA-level building blocks on index lists
 
@@ -1083,13 +1182,17 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_emit(SolveArgs a) {
     if (tid == 0) emit(0, carry.valid ? ~carry.k : n);  // before the first sound cut
 }
 
-// re-sort out[lo, lo + len) of one array by (key, row): the range is a union of sorted runs
+// re-sort out[lo, lo + len) of one array by (key, row): the range is a union of sorted runs. The
+// two index lists of the sort live in shared memory (sX, sY: SEAM_SMEM_IDX entries each) when the
+// range fits, else in the global scratch.
+constexpr uint32_t SEAM_SMEM_IDX = 8192;
 template <typename W>
 __device__ void repair_range(const SolveArgs &a, PolishSmem &sm, const Seg &sg, uint64_t lo,
-                             uint32_t len) {
+                             uint32_t len, uint32_t *sX, uint32_t *sY) {
     const int tid = threadIdx.x, dt = a.dtype;
     W *outk = reinterpret_cast<W *>(sg.keys);
-    uint32_t *X = a.g_x + sg.ebase + lo, *Y = a.g_y + sg.ebase + lo;
+    const bool onchip = len <= SEAM_SMEM_IDX;
+    uint32_t *X = onchip ? sX : a.g_x + sg.ebase + lo, *Y = onchip ? sY : a.g_y + sg.ebase + lo;
     for (uint32_t i = tid; i < len; i += SOLVE_THREADS) X[i] = i;
     __syncthreads();
     const W *rk = outk + lo;
@@ -1127,6 +1230,8 @@ template <typename W>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_fix(SolveArgs a) {
     extern __shared__ __align__(16) unsigned char sraw[];
     PolishSmem &sm = *reinterpret_cast<PolishSmem *>(sraw);
+    uint32_t *sX = reinterpret_cast<uint32_t *>(sraw + ((sizeof(PolishSmem) + 15) & ~(size_t)15));
+    uint32_t *sY = sX + SEAM_SMEM_IDX;
     __shared__ uint32_t sh_r;
     if (*a.err) return;
     const uint32_t nr = a.seam_cnt[0];
@@ -1137,7 +1242,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_fix(SolveArgs a) {
         __syncthreads();
         if (r >= nr) break;
         const SeamRange R = a.ranges[r];
-        repair_range<W>(a, sm, a.segs[R.seg], R.lo, (uint32_t)(R.hi - R.lo));
+        repair_range<W>(a, sm, a.segs[R.seg], R.lo, (uint32_t)(R.hi - R.lo), sX, sY);
     }
 }
 
@@ -1262,7 +1367,23 @@ cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s) {
     return a.key_bytes == 4 ? rounds_go<uint32_t>(a, s) : rounds_go<uint64_t>(a, s);
 }
 
+// k_finalize's scans for one array of more than one tile of buckets run on many blocks
+constexpr uint32_t MT_MIN_BUCKETS = MT_TILE + 1;
+
 cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s) {
+    const uint32_t nt = (a.NB + MT_TILE - 1) / MT_TILE;
+    if (a.nseg == 1 && a.NB >= MT_MIN_BUCKETS && nt <= MT_TILE &&
+        (uint64_t)nt * MAXR * sizeof(OKey) <= a.N * sizeof(uint32_t)) {
+        // tile maxima in the g_y scratch (free between the rounds and the polish)
+        OKey *agg = reinterpret_cast<OKey *>(a.g_y);
+        k_finalize_tiles<<<nt, MT_THREADS, 0, s>>>(a, agg);
+        cudaError_t e = nns_launched(cudaGetLastError());
+        if (e != cudaSuccess) return e;
+        k_finalize_prefix<<<1, MT_THREADS, 0, s>>>(a, agg, nt);
+        if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+        k_finalize_apply<<<nt, MT_THREADS, 0, s>>>(a, agg);
+        return nns_launched(cudaGetLastError());
+    }
     k_finalize<<<a.nseg, SCAN_THREADS, 0, s>>>(a);
     return nns_launched(cudaGetLastError());
 }
@@ -1290,7 +1411,11 @@ template <typename W> static cudaError_t seam_go(const SolveArgs &a, int sms, cu
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
     k_seam_emit<<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
-    k_seam_fix<W><<<2 * sms, SOLVE_THREADS, sizeof(PolishSmem), s>>>(a);
+    const size_t fix_smem = ((sizeof(PolishSmem) + 15) & ~(size_t)15) + 2 * sizeof(uint32_t) * SEAM_SMEM_IDX;
+    if ((e = cudaFuncSetAttribute(k_seam_fix<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fix_smem)) !=
+        cudaSuccess)
+        return e;
+    k_seam_fix<W><<<2 * sms, SOLVE_THREADS, fix_smem, s>>>(a);
     return nns_launched(cudaGetLastError());
 }
 cudaError_t launch_seam_repair(const SolveArgs &a, int sms, cudaStream_t s) {

@@ -237,6 +237,7 @@ extern "C" int nnsort_sort_noalloc(void *d_keys, int32_t *d_payload, uint64_t n,
     sa.g_flag = L.flag;
     sa.g_x = L.gx;
     sa.g_y = L.gy;
+    sa.N = n;
     sa.key_scratch = L.key[oi];
     sa.pay_scratch = pay ? L.pay[oi] : nullptr;
     sa.err = L.err;

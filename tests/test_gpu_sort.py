@@ -347,6 +347,44 @@ def test_seam_repairs_exactly_the_unsound_ranges(n, moves, far):
         assert cnt == 1 and elems > n - 4096
 
 
+def test_bucket_scans_on_many_blocks():
+    """Arrays of more than one tile of buckets run the scan over buckets that gives the polish its
+    carries per round on many blocks: output, per-round counts and out-of-order counts (which the
+    carries decide at every bucket boundary) equal the oracle's; the seam repairs of the same array
+    equal their definition."""
+    rs = np.random.RandomState(77)
+    n = 3_000_001  # 7,324 buckets of 2^9 positions: eight tiles of the scans
+    # distinct keys: without carried rows, ties between buckets are broken by in-bucket order, so
+    # the out-of-order counts equal the oracle's (which breaks them by row) only without ties
+    keys = rs.permutation(n).astype(np.float32)
+    L, _, _ = orc.nm_split(n)
+    rank = keys.astype(np.int64)
+    # near-sorted positions with collisions and a few keys moved thousands of positions: several
+    # rounds, out-of-order elements and carries across buckets
+    slots = (rank * 5 // 4 + rs.randint(-1, 2, n)).astype(np.int64)
+    idx = rs.choice(n, 300, replace=False)
+    slots[idx] += rs.randint(-3000, 3000, 300)
+    slots = np.clip(slots, 0, L - 1).astype(np.uint32)
+    dk, kt = to_dev(keys)
+    ds = torch.from_numpy(slots.view(np.int32)).cuda()
+    st = nns.sort(dk, None, None, eps=3, tau=0, slots=ds, key_type=kt, bucket_log2=9)
+    ok, _, ost, _ = orc.nnsort(keys, slots, L, 3, 0)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(ok))
+    assert stats_core(st) == stats_core(ost)
+    assert st["t"] >= 2 and sum(st["out_of_order"]) > 0
+    # seam: keys sent across bucket boundaries, every repair range as defined
+    slots2 = (rank * 5 // 4).astype(np.int64)
+    idx = rs.choice(n, 2000, replace=False)
+    slots2[idx] += rs.randint(-300, 300, 2000)
+    slots2 = np.clip(slots2, 0, L - 1).astype(np.uint32)
+    dk, kt = to_dev(keys)
+    ds = torch.from_numpy(slots2.view(np.int32)).cuda()
+    st2 = nns.sort(dk, None, None, slots=ds, key_type=kt, bucket_log2=9)
+    np.testing.assert_array_equal(bits(from_dev(dk, keys)), bits(np.sort(keys, kind="stable")))
+    assert (st2["repair_ranges"], st2["repaired"]) == _expected_seam(keys, slots2, 9)
+    assert st2["repair_ranges"] > 0
+
+
 def test_many_long_seam_ranges_sorted_together():
     """Five stretches of the key order mapped to positions in reverse: five unsound ranges of
     ~180K keys each (longer than one block repairs), separated by sound cuts, repaired by one packed
