@@ -403,9 +403,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_finalize(SolveArgs a) {
     }
 }
 
-// One large array: k_finalize's scans over tiles of MT_TILE buckets on many blocks, in three
-// launches (tile maxima; their exclusive prefix in one block; each tile's scan from its prefix).
-// Results equal the one-block scan's (the maximum is associative and exact).
+// One large array: the scans over its buckets (k_finalize's, k_seam_ps's) over tiles of MT_TILE
+// buckets on many blocks, in three launches (tile extrema; their exclusive prefix in one block;
+// each tile's scan from its prefix). Results equal the one-block scan's (the maximum is
+// associative and exact).
 constexpr int MT_THREADS = 256, MT_PER = 4;
 constexpr uint32_t MT_TILE = MT_THREADS * MT_PER;
 
@@ -1076,6 +1077,124 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_seam_ps(SolveArgs a) {
     }
 }
 
+// One large array: k_seam_ps over tiles of MT_TILE buckets on many blocks (tile extrema; their
+// exclusive suffix minimum / prefix maximum in one block; each tile's scans from them).
+// agg[2 i] = inverted minimum of tile i's non-empty buckets (blo), agg[2 i + 1] = their maximum (bhi)
+__global__ void __launch_bounds__(MT_THREADS) k_seam_tiles(SolveArgs a, OKey *agg) {
+    __shared__ KMax scratch[33];
+    __shared__ KMax tot;
+    if (*a.err) return;
+    const int tid = threadIdx.x;
+    const Seg &sg = a.segs[0];
+    const uint32_t c0 = blockIdx.x * MT_TILE + (uint32_t)tid * MT_PER;
+    KMax lo = kmax_none(), hi = kmax_none();
+#pragma unroll
+    for (int k = 0; k < MT_PER; ++k) {
+        const uint32_t c = c0 + k;
+        if (c < sg.nb) {
+            const uint32_t bi = sg.bbase + c;
+            if (a.bstart[bi + 1] > a.bstart[bi]) {
+                lo = kmax(lo, kinv(kmax_of(a.blo[bi])));
+                hi = kmax(hi, kmax_of(a.bhi[bi]));
+            }
+        }
+    }
+    block_excl_max(lo, scratch, &tot);
+    if (tid == 0) agg[2 * (size_t)blockIdx.x] = okey_of_kmax(tot);
+    block_excl_max(hi, scratch, &tot);
+    if (tid == 0) agg[2 * (size_t)blockIdx.x + 1] = okey_of_kmax(tot);
+}
+// agg[2 i] <- inverted minimum over the tiles after i; agg[2 i + 1] <- maximum over the tiles before i
+__global__ void __launch_bounds__(MT_THREADS) k_seam_prefix(SolveArgs a, OKey *agg, uint32_t ntiles) {
+    __shared__ KMax scratch[33];
+    if (*a.err) return;
+    const int tid = threadIdx.x;
+    {   // suffix: thread tid takes tiles ntiles - 1 - (tid * MT_PER + k)
+        KMax v[MT_PER], loc = kmax_none();
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t r = (uint32_t)tid * MT_PER + k;
+            v[k] = r < ntiles ? kmax_of(agg[2 * (size_t)(ntiles - 1 - r)]) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = block_excl_max(loc, scratch, nullptr);
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t r = (uint32_t)tid * MT_PER + k;
+            if (r < ntiles) agg[2 * (size_t)(ntiles - 1 - r)] = okey_of_kmax(run);
+            run = kmax(run, v[k]);
+        }
+    }
+    {
+        KMax v[MT_PER], loc = kmax_none();
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t i = (uint32_t)tid * MT_PER + k;
+            v[k] = i < ntiles ? kmax_of(agg[2 * (size_t)i + 1]) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = block_excl_max(loc, scratch, nullptr);
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t i = (uint32_t)tid * MT_PER + k;
+            if (i < ntiles) agg[2 * (size_t)i + 1] = okey_of_kmax(run);
+            run = kmax(run, v[k]);
+        }
+    }
+}
+__global__ void __launch_bounds__(MT_THREADS) k_seam_apply(SolveArgs a, const OKey *agg) {
+    __shared__ KMax scratch[33];
+    if (*a.err) return;
+    const int tid = threadIdx.x;
+    const Seg &sg = a.segs[0];
+    const uint32_t t0 = blockIdx.x * MT_TILE;
+    const uint32_t t1 = std::min<uint32_t>(sg.nb, t0 + MT_TILE);
+    {   // S(b): thread tid takes the tile's buckets t1 - 1 - (tid * MT_PER + k), later ones first
+        KMax v[MT_PER], loc = kmax_none();
+        uint32_t nem = 0;
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t r = (uint32_t)tid * MT_PER + k;
+            const bool own = r < t1 - t0;
+            const uint32_t bi = sg.bbase + (own ? t1 - 1 - r : 0u);
+            const bool ne = own && a.bstart[bi + 1] > a.bstart[bi];
+            nem |= (ne ? 1u : 0u) << k;
+            v[k] = ne ? kinv(kmax_of(a.blo[bi])) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = kmax(kmax_of(agg[2 * (size_t)blockIdx.x]), block_excl_max(loc, scratch, nullptr));
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            if ((nem >> k) & 1u) {
+                a.seam_suf[sg.bbase + t1 - 1 - ((uint32_t)tid * MT_PER + k)] = okey_of_kmax(kinv(run));
+                run = kmax(run, v[k]);
+            }
+        }
+    }
+    {   // P(b)
+        KMax v[MT_PER], loc = kmax_none();
+        uint32_t nem = 0;
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            const uint32_t c = t0 + (uint32_t)tid * MT_PER + k;
+            const bool own = c < t1;
+            const uint32_t bi = sg.bbase + (own ? c : 0u);
+            const bool ne = own && a.bstart[bi + 1] > a.bstart[bi];
+            nem |= (ne ? 1u : 0u) << k;
+            v[k] = ne ? kmax_of(a.bhi[bi]) : kmax_none();
+            loc = kmax(loc, v[k]);
+        }
+        KMax run = kmax(kmax_of(agg[2 * (size_t)blockIdx.x + 1]), block_excl_max(loc, scratch, nullptr));
+#pragma unroll
+        for (int k = 0; k < MT_PER; ++k) {
+            if ((nem >> k) & 1u) {
+                a.seam_pre[sg.bbase + t0 + (uint32_t)tid * MT_PER + k] = okey_of_kmax(run);
+                run = kmax(run, v[k]);
+            }
+        }
+    }
+}
+
 // 2) k_seam_cuts (one thread per bucket of every array): the bucket's first and last sound cut.
 template <typename W>
 __global__ void k_seam_cuts(SolveArgs a) {
@@ -1367,7 +1486,7 @@ cudaError_t launch_rounds(const SolveArgs &a, cudaStream_t s) {
     return a.key_bytes == 4 ? rounds_go<uint32_t>(a, s) : rounds_go<uint64_t>(a, s);
 }
 
-// k_finalize's scans for one array of more than one tile of buckets run on many blocks
+// the scans of one array of more than one tile of buckets run on many blocks
 constexpr uint32_t MT_MIN_BUCKETS = MT_TILE + 1;
 
 cudaError_t launch_finalize(const SolveArgs &a, cudaStream_t s) {
@@ -1405,7 +1524,18 @@ cudaError_t launch_polish(const SolveArgs &a, cudaStream_t s) {
 template <typename W> static cudaError_t seam_go(const SolveArgs &a, int sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.seam_cnt, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_seam_ps<<<a.nseg, SCAN_THREADS, 0, s>>>(a);
+    const uint32_t nt = (a.NB + MT_TILE - 1) / MT_TILE;
+    if (a.nseg == 1 && a.NB >= MT_MIN_BUCKETS && nt <= MT_TILE) {
+        // tile extrema in the cut scratch (free until k_seam_cuts): 2 nt <= 2 NB entries of 16 bytes
+        OKey *agg = reinterpret_cast<OKey *>(a.seam_cut);
+        k_seam_tiles<<<nt, MT_THREADS, 0, s>>>(a, agg);
+        if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+        k_seam_prefix<<<1, MT_THREADS, 0, s>>>(a, agg, nt);
+        if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
+        k_seam_apply<<<nt, MT_THREADS, 0, s>>>(a, agg);
+    } else {
+        k_seam_ps<<<a.nseg, SCAN_THREADS, 0, s>>>(a);
+    }
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
     k_seam_cuts<W><<<(a.NB + 255) / 256, 256, 0, s>>>(a);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;

@@ -348,10 +348,10 @@ def test_seam_repairs_exactly_the_unsound_ranges(n, moves, far):
 
 
 def test_bucket_scans_on_many_blocks():
-    """Arrays of more than one tile of buckets run the scan over buckets that gives the polish its
-    carries per round on many blocks: output, per-round counts and out-of-order counts (which the
-    carries decide at every bucket boundary) equal the oracle's; the seam repairs of the same array
-    equal their definition."""
+    """Arrays of more than one tile of buckets run the scans over buckets (the polish's carries per
+    round, the seam's prefix maxima and suffix minima) on many blocks: output, per-round counts and
+    out-of-order counts (which the carries decide at every bucket boundary) equal the oracle's, and
+    the seam repairs equal their definition."""
     rs = np.random.RandomState(77)
     n = 3_000_001  # 7,324 buckets of 2^9 positions: eight tiles of the scans
     # distinct keys: without carried rows, ties between buckets are broken by in-bucket order, so
