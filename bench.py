@@ -45,7 +45,7 @@ WORKLOAD = ("268,435,456 float32 keys lognormal(0,2) with 5% exact duplicates, k
 # the launch) from single-kernel ncu captures at 2^26 keys of the same distribution and model
 # recipe; traffic grows in proportion to the keys. A kernel changed since its capture has no entry.
 TRAFFIC_PER_KEY = {
-    ("predict", "bf16x2"): 7.366,   # k_predict_bf16_mg<64, split>
+    ("predict", "bf16x2"): 7.363,   # k_predict_bf16_mg<64, split>
     ("partition", None): 19.78,     # per pass: k_tile_hist 4.22 + k_scatter 15.56
     ("rounds", None): 6.80,         # k_rounds
     ("polish", None): 12.66,        # k_polish
