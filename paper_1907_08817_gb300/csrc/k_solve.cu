@@ -588,28 +588,33 @@ __device__ Idx *cta_radix_sort(Idx *src, Idx *dst, uint32_t cnt, int keybits, Ke
     return src;
 }
 
-// Stable sort of an index list by a 32- or 64-bit key in one counting pass, for lists whose keys
-// spread evenly over their range (a bucket's elements under a fitted model). The range
-// [kmin, kmax] is cut into NBIN bins of 2^s consecutive key values; every element drops into its
-// bin (shared-memory atomics, so in arbitrary order inside it), and each element's place inside its
-// bin is then the number of the bin's elements before it in (key, index) order -- counts that are
-// independent of one another, so all threads rank their elements at once. `src` must list indices
-// in increasing order, so that index order is list order and the result is stable. Returns the
-// buffer holding the result (src), or nullptr, having changed neither list, when some bin would
-// hold more than BIN_MAX elements (the caller then sorts by radix).
+// Stable sort of the element indices 0..cnt-1 by a 32- or 64-bit key in one counting pass, for
+// lists whose keys spread evenly over their range (a bucket's elements under a fitted model). The
+// order is that of the composite key c(i) = (key(i) - kmin) * 2^ib + i (ib = bits of cnt - 1):
+// (key, index) order, i.e. a stable sort. Its range is cut into NBIN bins of 2^s consecutive
+// values; when the keys span few distinct values (binary32 keys near a density peak repeat
+// often) the index's top bits split each value's elements over several bins instead of crowding
+// one. Every element drops into its bin (shared-memory atomics, so in arbitrary order inside
+// it), and each element's place inside its bin is then the number of the bin's elements before it
+// in (key, index) order -- counts that are independent of one another, so all threads rank their
+// elements at once. The result is left in `src` (`dst` is scratch), and src is returned; nullptr,
+// with neither list touched, when some bin would hold more than BIN_MAX elements (the caller then
+// sorts by radix).
 constexpr uint32_t NBIN = 4096;
+constexpr int NBIN_LOG = 12;
 constexpr uint32_t BIN_MAX = 24;
 constexpr uint32_t BIN_SORT_MAX = 6144;  // longest list sorted this way (1.5 elements per bin)
 template <typename Idx, typename KeyFn>
 __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_t *bins /*[NBIN]*/,
                              unsigned long long *mm /*[2 * SNW]*/, uint32_t *scratch /*33*/) {
     static_assert(NBIN % SOLVE_THREADS == 0, "whole bins per thread");
+    static_assert(NBIN == (1u << NBIN_LOG), "NBIN is 2^NBIN_LOG");
     constexpr int BPT = NBIN / SOLVE_THREADS;
-    using K = decltype(kf(src[0]));  // the key's own unsigned width
+    using K = decltype(kf((Idx)0));  // the key's own unsigned width
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     K lo = (K)~(K)0, hi = 0;
     for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
-        const K k = kf(src[i]);
+        const K k = kf((Idx)i);
         lo = k < lo ? k : lo;
         hi = k > hi ? k : hi;
     }
@@ -630,14 +635,20 @@ __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_
         lo = (K)mm[q] < lo ? (K)mm[q] : lo;
         hi = (K)mm[SNW + q] > hi ? (K)mm[SNW + q] : hi;
     }
+    // c(i) < 2^(br + ib) with br = bits of (kmax - kmin); bin = c >> sh with sh = max(0, br + ib -
+    // NBIN_LOG). With d = sh - ib >= 0 the index bits fall off entirely: bin = (key - kmin) >> d;
+    // otherwise bin = ((key - kmin) << -d) | (i >> sh), both below NBIN.
     const K range = hi - lo;
-    int sh = 0;  // (range >> sh) < NBIN
-    if (range >= NBIN) {
-        if constexpr (sizeof(K) == 8) sh = (64 - __clzll((long long)range)) - 12;
-        else sh = (32 - __clz((int)range)) - 12;
-    }
-    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS)
-        atomicAdd(&bins[(uint32_t)((kf(src[i]) - lo) >> sh)], 1u);
+    int br = 0;
+    if constexpr (sizeof(K) == 8) br = range ? 64 - __clzll((long long)range) : 0;
+    else br = range ? 32 - __clz((int)range) : 0;
+    const int ib = cnt > 1 ? 32 - __clz((int)(cnt - 1)) : 0;
+    const int sh = br + ib > NBIN_LOG ? br + ib - NBIN_LOG : 0;
+    const int d = sh - ib;
+    auto bin_of = [&](uint32_t i, K k) -> uint32_t {
+        return d >= 0 ? (uint32_t)((K)(k - lo) >> d) : (((uint32_t)(k - lo) << -d) | (i >> sh));
+    };
+    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) atomicAdd(&bins[bin_of(i, kf((Idx)i))], 1u);
     __syncthreads();
     uint32_t tsum = 0, tmax = 0;
 #pragma unroll
@@ -655,23 +666,23 @@ __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_
         run += c;
     }
     __syncthreads();
-    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
-        const Idx x = src[i];
-        dst[atomicAdd(&bins[(uint32_t)((kf(x) - lo) >> sh)], 1u)] = x;
-    }
+    for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS)
+        dst[atomicAdd(&bins[bin_of(i, kf((Idx)i))], 1u)] = (Idx)i;
     __syncthreads();
     // bins[b] is now one past the last slot of bin b; each element's rank inside its bin gives its
-    // slot, written back to src (whose identity list is no longer needed)
+    // slot in src
     for (uint32_t j = tid; j < cnt; j += SOLVE_THREADS) {
         const Idx x = dst[j];
         const K kx = kf(x);
-        const uint32_t b = (uint32_t)((kx - lo) >> sh);
+        const uint32_t b = bin_of((uint32_t)x, kx);
         const uint32_t st = b ? bins[b - 1] : 0u, e = bins[b];
         uint32_t r = 0;
-        for (uint32_t i = st; i < e; ++i) {
-            const Idx y = dst[i];
-            const K ky = kf(y);
-            r += (ky < kx || (ky == kx && y < x)) ? 1u : 0u;
+        if (e - st > 1) {
+            for (uint32_t i = st; i < e; ++i) {
+                const Idx y = dst[i];
+                const K ky = kf(y);
+                r += (ky < kx || (ky == kx && y < x)) ? 1u : 0u;
+            }
         }
         src[st + r] = x;
     }
@@ -731,6 +742,32 @@ struct BucketView {
     }
 };
 
+// Block-wide exclusive prefix maximum of one u64 per thread (0 where no thread before holds
+// more). Ends without a barrier: the caller passes at least one __syncthreads() before it writes
+// `scratch` again.
+__device__ __forceinline__ unsigned long long block_excl_max_u64(unsigned long long v,
+                                                                 unsigned long long *scratch /*SNW*/) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x = y > x ? y : x;
+    }
+    unsigned long long ex = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+    if (lane == 0) ex = 0;
+    if (lane == 31) scratch[wid] = x;
+    __syncthreads();
+    // every warp folds the totals of the warps before it
+    unsigned long long m = lane < wid ? scratch[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+        m = y > m ? y : m;
+    }
+    return m > ex ? m : ex;
+}
+
 // Fig. "Algorithm polish", first part: for each o_r its stored elements in position order and the
 // out-of-order split against the running maximum (carry from earlier buckets first); the in-order
 // rest is the run R_r. Sets v.F for leftover elements (last conflict array and out-of-order ones)
@@ -764,6 +801,10 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
         sm.carry[tid].valid = cr.valid;
     }
     __syncthreads();
+    // 32-bit keys with a position table of at most NBIN entries keep each stored element's order
+    // image beside its index in the table (the bin counters, idle until the bucket sort)
+    const bool packed = sizeof(W) == 4 && Wn <= NBIN;
+    uint32_t *TK = sm.bins;
     for (int r = 0; r < t; ++r) {
         // o_r: stored elements in position order
         for (uint32_t j = tid; j < Wn; j += SOLVE_THREADS) v.TB[j] = EMPTY;
@@ -777,34 +818,65 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
             }
 #pragma unroll
             for (int q = 0; q < LB; ++q)
-                if (pv[q] != 0xFFFFFFFFu) v.TB[pv[q]] = (Idx)(i0 + q * SOLVE_THREADS + tid);
+                if (pv[q] != 0xFFFFFFFFu) {
+                    const uint32_t i = i0 + q * SOLVE_THREADS + tid;
+                    v.TB[pv[q]] = (Idx)i;
+                    if (packed) TK[pv[q]] = (uint32_t)v.ok(i);
+                }
         }
         __syncthreads();
+        // out-of-order split against the running maximum (carry from earlier buckets first), run
+        // over the position table itself: each thread takes a contiguous range of positions, so
+        // thread order is position order
         const uint32_t per_s = (Wn + SOLVE_THREADS - 1) / SOLVE_THREADS;
         const uint32_t p0 = std::min(Wn, tid * per_s), p1 = std::min(Wn, p0 + per_s);
-        uint32_t c = 0;
-        for (uint32_t j = p0; j < p1; ++j) c += (v.TB[j] != EMPTY);
-        uint32_t nseq;
-        uint32_t o = block_excl_sum(c, sm.scratch, &nseq);
-        for (uint32_t j = p0; j < p1; ++j)
-            if (v.TB[j] != EMPTY) v.Y[o++] = v.TB[j];
-        __syncthreads();
-        // out-of-order split against the running maximum (carry from earlier buckets first)
-        const uint32_t per = (nseq + SOLVE_THREADS - 1) / SOLVE_THREADS;
-        const uint32_t q0 = std::min(nseq, tid * per), q1 = std::min(nseq, q0 + per);
+        if (packed) {
+            // (order image, tie-break) packed as order image * 2^32 + tie-break: the pair order is
+            // the integer order, and (0, 0) -- the least pair -- stands for "none", which leaves
+            // every maximum and every out-of-order test unchanged
+            unsigned long long loc = 0;
+#pragma unroll 8
+            for (uint32_t j = p0; j < p1; ++j) {
+                const Idx x = v.TB[j];
+                if (x == EMPTY) continue;
+                const unsigned long long e = ((unsigned long long)TK[j] << 32) | v.tb(x);
+                loc = e > loc ? e : loc;
+            }
+            unsigned long long run =
+                block_excl_max_u64(loc, reinterpret_cast<unsigned long long *>(sm.kscratch));
+            const KMax cr = sm.carry[r];
+            const unsigned long long cp = cr.valid ? ((cr.k << 32) | cr.tb) : 0ull;
+            run = cp > run ? cp : run;
+            uint32_t evicted = 0;
+#pragma unroll 8
+            for (uint32_t j = p0; j < p1; ++j) {
+                const Idx x = v.TB[j];
+                if (x == EMPTY) continue;
+                const unsigned long long e = ((unsigned long long)TK[j] << 32) | v.tb(x);
+                if (e < run) {
+                    v.F[x] = 1;
+                    ++evicted;
+                } else {
+                    run = e;
+                }
+            }
+            if (evicted) atomicAdd(&sm.ooo[r], evicted);
+            __syncthreads();
+            continue;
+        }
         KMax loc = kmax_none();
-        for (uint32_t q = q0; q < q1; ++q) {
-            const uint32_t x = v.Y[q];
+        for (uint32_t j = p0; j < p1; ++j) {
+            const Idx x = v.TB[j];
+            if (x == EMPTY) continue;
             KMax e; e.k = v.ok(x); e.tb = v.tb(x); e.valid = 1;
             loc = kmax(loc, e);
         }
         KMax run = block_excl_max(loc, sm.kscratch, nullptr);
-        {
-            run = kmax(sm.carry[r], run);
-        }
+        run = kmax(sm.carry[r], run);
         uint32_t evicted = 0;
-        for (uint32_t q = q0; q < q1; ++q) {
-            const uint32_t x = v.Y[q];
+        for (uint32_t j = p0; j < p1; ++j) {
+            const Idx x = v.TB[j];
+            if (x == EMPTY) continue;
             const unsigned long long xk = v.ok(x);
             const uint32_t xt = v.tb(x);
             if (run.valid && okey_less(xk, xt, run.k, run.tb)) {
@@ -830,12 +902,14 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
     // sorted by QuickSort(w) and merged with the in-order runs R_1..R_t of Fig. "Algorithm polish" --
     // is all of its elements in (key, row) order, so it is computed as one stable sort of the whole
     // bucket; the runs above supply the out-of-order counts and the fates.
-    for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.X[i] = (Idx)i;
-    __syncthreads();
     auto kf = [&](Idx x) { return v.ok(x); };
     Idx *A = nbk <= BIN_SORT_MAX ? cta_bin_sort<Idx>(v.X, v.Y, nbk, kf, sm.bins, sm.mm, sm.scratch)
                                  : nullptr;
-    if (!A) A = cta_radix_sort<Idx>(v.X, v.Y, nbk, keybits, kf, sm.hist, sm.wcnt, sm.scratch);
+    if (!A) {
+        for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.X[i] = (Idx)i;
+        __syncthreads();
+        A = cta_radix_sort<Idx>(v.X, v.Y, nbk, keybits, kf, sm.hist, sm.wcnt, sm.scratch);
+    }
     __syncthreads();
     // write the bucket's sorted run in place of the caller's array
     const uint64_t off = (uint64_t)s0 - sg.ebase;
