@@ -599,14 +599,19 @@ __device__ Idx *cta_radix_sort(Idx *src, Idx *dst, uint32_t cnt, int keybits, Ke
 // in (key, index) order -- counts that are independent of one another, so all threads rank their
 // elements at once. The result is left in `src` (`dst` is scratch), and src is returned; nullptr,
 // with neither list touched, when some bin would hold more than BIN_MAX elements (the caller then
-// sorts by radix).
+// sorts by radix). For 16-bit index lists the caller may pass `pair`, room for one u32 per element,
+// and `out16`: when every bin's keys differ in at most their low 16 bits, the scatter stores each
+// element as (its key's offset inside the bin) * 2^16 + index -- a word whose integer order is the
+// (key, index) order inside the bin -- so the ranking compares words without reading keys, and
+// the result is left in out16 (returned) instead of src.
 constexpr uint32_t NBIN = 4096;
 constexpr int NBIN_LOG = 12;
 constexpr uint32_t BIN_MAX = 24;
 constexpr uint32_t BIN_SORT_MAX = 6144;  // longest list sorted this way (1.5 elements per bin)
 template <typename Idx, typename KeyFn>
 __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_t *bins /*[NBIN]*/,
-                             unsigned long long *mm /*[2 * SNW]*/, uint32_t *scratch /*33*/) {
+                             unsigned long long *mm /*[2 * SNW]*/, uint32_t *scratch /*33*/,
+                             uint32_t *pair = nullptr, uint16_t *out16 = nullptr) {
     static_assert(NBIN % SOLVE_THREADS == 0, "whole bins per thread");
     static_assert(NBIN == (1u << NBIN_LOG), "NBIN is 2^NBIN_LOG");
     constexpr int BPT = NBIN / SOLVE_THREADS;
@@ -666,6 +671,29 @@ __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_
         run += c;
     }
     __syncthreads();
+    if constexpr (sizeof(Idx) == 2) {
+        if (pair && out16 && d <= 16) {
+            // inside bin b the keys share (key - kmin) >> d = b (d >= 0) or are all equal (d < 0)
+            const uint32_t rmask = d > 0 ? (1u << d) - 1u : 0u;
+            for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
+                const K k = kf((Idx)i);
+                const uint32_t res = (uint32_t)(K)(k - lo) & rmask;
+                pair[atomicAdd(&bins[bin_of(i, k)], 1u)] = (res << 16) | i;
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < cnt; j += SOLVE_THREADS) {
+                const uint32_t c = pair[j];
+                const uint32_t x = c & 0xFFFFu;
+                const uint32_t b = bin_of(x, kf((Idx)x));
+                const uint32_t st = b ? bins[b - 1] : 0u, e = bins[b];
+                uint32_t r = 0;
+                for (uint32_t i = st; i < e; ++i) r += pair[i] < c ? 1u : 0u;
+                out16[st + r] = (uint16_t)x;
+            }
+            __syncthreads();
+            return reinterpret_cast<Idx *>(out16);
+        }
+    }
     for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS)
         dst[atomicAdd(&bins[bin_of(i, kf((Idx)i))], 1u)] = (Idx)i;
     __syncthreads();
@@ -893,7 +921,8 @@ __device__ void polish_runs(const SolveArgs &a, PolishSmem &sm, const BucketView
 
 template <typename W, typename Idx, bool FL>
 __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketView<W, Idx, FL> &v,
-                              uint32_t b, uint32_t s0, uint32_t nbk, const Seg &sg) {
+                              uint32_t b, uint32_t s0, uint32_t nbk, const Seg &sg,
+                              uint32_t *pair, uint16_t *out16) {
     const int tid = threadIdx.x;
     const int t = sm.t;
     const int keybits = (a.key_bytes == 4) ? 32 : 64;
@@ -903,7 +932,7 @@ __device__ void polish_bucket(const SolveArgs &a, PolishSmem &sm, const BucketVi
     // is all of its elements in (key, row) order, so it is computed as one stable sort of the whole
     // bucket; the runs above supply the out-of-order counts and the fates.
     auto kf = [&](Idx x) { return v.ok(x); };
-    Idx *A = nbk <= BIN_SORT_MAX ? cta_bin_sort<Idx>(v.X, v.Y, nbk, kf, sm.bins, sm.mm, sm.scratch)
+    Idx *A = nbk <= BIN_SORT_MAX ? cta_bin_sort<Idx>(v.X, v.Y, nbk, kf, sm.bins, sm.mm, sm.scratch, pair, out16)
                                  : nullptr;
     if (!A) {
         for (uint32_t i = tid; i < nbk; i += SOLVE_THREADS) v.X[i] = (Idx)i;
@@ -1040,7 +1069,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
         }
         __syncthreads();
         BucketView<W, uint16_t, FL> v{K, S16, nullptr, R, F, P, T, X, Y, TB, Wn - 1u};
-        polish_bucket<W, uint16_t, FL>(a, sm, v, b, s0, nbk, sg);
+        // X and Y are adjacent: together one u32 per element for the bucket sort's packed words;
+        // the result goes to S16, idle once the runs are split
+        polish_bucket<W, uint16_t, FL>(a, sm, v, b, s0, nbk, sg, reinterpret_cast<uint32_t *>(X), S16);
     } else {
         if (tid == 0) atomicAdd(&a.stats[sm.seg].oversized, 1u);
         uint32_t *TB = reinterpret_cast<uint32_t *>(dyn);
@@ -1048,7 +1079,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_polish(SolveArgs a) {
                                       a.rank + s0, a.g_flag + s0, a.pay ? a.pay + s0 : nullptr,
                                       a.rows ? a.rows + s0 : nullptr, a.g_x + s0, a.g_y + s0,
                                       TB, Wn - 1u};
-        polish_bucket<W, uint32_t, FL>(a, sm, v, b, s0, nbk, sg);
+        polish_bucket<W, uint32_t, FL>(a, sm, v, b, s0, nbk, sg, nullptr, nullptr);
     }
 }
 
