@@ -673,18 +673,31 @@ __device__ Idx *cta_bin_sort(Idx *src, Idx *dst, uint32_t cnt, KeyFn kf, uint32_
     __syncthreads();
     if constexpr (sizeof(Idx) == 2) {
         if (pair && out16 && d <= 16) {
-            // inside bin b the keys share (key - kmin) >> d = b (d >= 0) or are all equal (d < 0)
-            const uint32_t rmask = d > 0 ? (1u << d) - 1u : 0u;
+            // inside bin b the keys share (key - kmin) >> d = b (d >= 0) or are all equal (d < 0).
+            // When the offset's bits and the index's fit in 32 - NBIN_LOG, the word also carries
+            // the bin: bin * 2^20 + offset * 2^ib + index; otherwise offset * 2^16 + index.
+            const int dres = d > 0 ? d : 0;
+            const bool full = dres + ib <= 32 - NBIN_LOG;
+            const uint32_t rmask = dres ? (1u << dres) - 1u : 0u;
+            const uint32_t imask = (1u << ib) - 1u;
             for (uint32_t i = tid; i < cnt; i += SOLVE_THREADS) {
                 const K k = kf((Idx)i);
+                const uint32_t b = bin_of(i, k);
                 const uint32_t res = (uint32_t)(K)(k - lo) & rmask;
-                pair[atomicAdd(&bins[bin_of(i, k)], 1u)] = (res << 16) | i;
+                pair[atomicAdd(&bins[b], 1u)] =
+                    full ? (b << (32 - NBIN_LOG)) | (res << ib) | i : (res << 16) | i;
             }
             __syncthreads();
             for (uint32_t j = tid; j < cnt; j += SOLVE_THREADS) {
                 const uint32_t c = pair[j];
-                const uint32_t x = c & 0xFFFFu;
-                const uint32_t b = bin_of(x, kf((Idx)x));
+                uint32_t x, b;
+                if (full) {
+                    x = c & imask;
+                    b = c >> (32 - NBIN_LOG);
+                } else {
+                    x = c & 0xFFFFu;
+                    b = bin_of(x, kf((Idx)x));
+                }
                 const uint32_t st = b ? bins[b - 1] : 0u, e = bins[b];
                 uint32_t r = 0;
                 for (uint32_t i = st; i < e; ++i) r += pair[i] < c ? 1u : 0u;
