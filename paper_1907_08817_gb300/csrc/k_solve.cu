@@ -55,6 +55,18 @@ template <typename W> __device__ __forceinline__ W ldk(const void *p, size_t i) 
 }
 
 __device__ __forceinline__ KMax kmax_none() { KMax r; r.k = 0; r.tb = 0; r.valid = 0; return r; }
+// maximum over the 32 lanes of a warp (every lane gets it)
+__device__ __forceinline__ KMax warp_max_kmax(KMax v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        KMax y;
+        y.k = __shfl_xor_sync(0xFFFFFFFFu, v.k, o);
+        y.tb = __shfl_xor_sync(0xFFFFFFFFu, v.tb, o);
+        y.valid = __shfl_xor_sync(0xFFFFFFFFu, v.valid, o);
+        v = kmax(v, y);
+    }
+    return v;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Bucket order for the per-bucket kernels: blocks are dispatched roughly in index order, so heavy
@@ -223,8 +235,7 @@ __host__ __device__ constexpr size_t rounds_smem(int wlog) {
 template <typename W>
 __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
     extern __shared__ uint32_t tbl[];  // Wn claims | rcap local positions (u16) | rcap round indices (u8)
-    __shared__ KMax ks[33];
-    __shared__ KMax tot;
+    __shared__ KMax ks[RT / 32];
     __shared__ unsigned int red_cnt[RT / 32];
     __shared__ int sh_seg;
     const int tid = threadIdx.x;
@@ -266,8 +277,13 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
     __syncthreads();
     auto lpos = [&](uint32_t i) -> uint32_t { return onchip ? (uint32_t)pos[i] : (a.gs[s0 + i] & wm); };
     // Algorithm NN-sort: in iteration r every element still unplaced claims its position; the
-    // lowest row (first arrival) is stored, the others move on to the next conflict array
-    for (int r = 0; r < eps; ++r) {
+    // lowest row (first arrival) is stored, the others move on to the next conflict array. The
+    // check that moves the others on also counts the stored elements and takes the largest of them
+    // (for the polish carry).
+    const int lane = tid & 31, wid = tid >> 5;
+    unsigned long long ge = nbk;  // elements whose round index is >= r
+    int r = 0;
+    for (; r < eps; ++r) {
         for (uint32_t j = tid; j < Wn; j += RT) tbl[j] = EMPTY32;
         __syncthreads();
         // every claimant issues a shared-memory atomicMin of its row (the lowest row wins); a warp
@@ -289,6 +305,8 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
         }
         __syncthreads();
         int left = 0;
+        unsigned int cnt = 0;
+        KMax m = kmax_none();
         for (uint32_t i0 = 0; i0 < nbk; i0 += RT * LB) {
             uint32_t pv[LB];
 #pragma unroll
@@ -296,31 +314,22 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
                 const uint32_t i = i0 + q * RT + tid;
                 pv[q] = (i < nbk && cur[i] == r) ? lpos(i) : EMPTY32;
             }
+            bool win[LB];
 #pragma unroll
             for (int q = 0; q < LB; ++q) {
                 const uint32_t i = i0 + q * RT + tid;
-                if (pv[q] != EMPTY32 && tbl[pv[q]] != i) { cur[i] = (uint8_t)(r + 1); left = 1; }
+                win[q] = false;
+                if (pv[q] != EMPTY32) {
+                    if (tbl[pv[q]] != i) { cur[i] = (uint8_t)(r + 1); left = 1; }
+                    else win[q] = true;
+                }
             }
-        }
-        if (__syncthreads_or(left) == 0) break;
-    }
-    // per iteration: how many elements it stored and the largest of them (for the polish carry)
-    unsigned long long ge = nbk;  // elements whose round index is >= r
-    for (int r = 0; r < eps; ++r) {
-        KMax m = kmax_none();
-        unsigned int cnt = 0;
-        for (uint32_t i0 = 0; i0 < nbk; i0 += RT * LB) {
             W kv[LB];
-            bool hit[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) kv[q] = win[q] ? ldk<W>(a.keys, s0 + i0 + q * RT + tid) : (W)0;
 #pragma unroll
             for (int q = 0; q < LB; ++q) {
-                const uint32_t i = i0 + q * RT + tid;
-                hit[q] = i < nbk && cur[i] == r;
-                kv[q] = hit[q] ? ldk<W>(a.keys, s0 + i) : (W)0;
-            }
-#pragma unroll
-            for (int q = 0; q < LB; ++q) {
-                if (!hit[q]) continue;
+                if (!win[q]) continue;
                 const uint32_t i = i0 + q * RT + tid;
                 KMax x;
                 x.k = ordbits(word64(kv[q]), dt);
@@ -331,18 +340,25 @@ __global__ void __launch_bounds__(RT, 4) k_rounds(SolveArgs a) {
             }
         }
         cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-        if ((tid & 31) == 0) red_cnt[tid >> 5] = cnt;
-        block_excl_max(m, ks, &tot);  // ends with a barrier: red_cnt and tot are complete
+        m = warp_max_kmax(m);
+        if (lane == 0) { red_cnt[wid] = cnt; ks[wid] = m; }
+        // a barrier as well: red_cnt and ks are complete (they are written again only after the
+        // next iteration's barriers)
+        const bool more = __syncthreads_or(left) != 0;
         if (tid == 0) {
             unsigned int c = 0;
-            for (int w = 0; w < RT / 32; ++w) c += red_cnt[w];
+            KMax t = kmax_none();
+            for (int w = 0; w < RT / 32; ++w) { c += red_cnt[w]; t = kmax(t, ks[w]); }
             ge -= c;
             if (ge) atomicAdd(&a.stats[seg].count_ge[r + 1], ge);
-            OKey o; o.k = tot.k; o.tb = tot.tb; o.valid = tot.valid;
+            OKey o; o.k = t.k; o.tb = t.tb; o.valid = t.valid;
             a.bmax[(size_t)b * MAXR + r] = o;
         }
-        __syncthreads();
+        if (!more) { ++r; break; }
     }
+    // iterations after the last one that stored anything store nothing
+    for (; r < eps; ++r)
+        if (tid == 0) { OKey z; z.k = 0; z.tb = 0; z.valid = 0; a.bmax[(size_t)b * MAXR + r] = z; }
     if (onchip)
         for (uint32_t i = tid; i < nbk; i += RT) a.rank[s0 + i] = cur[i];
 }
