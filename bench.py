@@ -846,6 +846,50 @@ def cpu_sorts(host, cap=16_777_216):
 
 
 # --------------------------------------------------------------------------- GPU arm
+def _bf16_rn(a):
+    """binary32 -> BF16 (round to nearest even), returned as binary32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def w2_split_displacement(keys_sample, desc, params, nm):
+    """Where the split-BF16 form's displacement comes from, on a host sample of keys (two-layer
+    models, float32 keys, order-image translate): F(x) in binary64 with the split form's operands --
+    each first-layer activation as a BF16 part (truncated) plus an FP16 rest, W2 as the kernel stages
+    it (BF16 for the BF16 part, FP16 for the rest) -- against F(x) with W2 carried as a BF16 part
+    plus a BF16 rest, and against exact W2; each against the binary64 model on the same inputs.
+    Displacements are |dF| * n * m (positions)."""
+    h1, h2 = desc["h1"], desc["h2"]
+    p = params.astype(np.float64)
+    W1, b1 = p[:h1], p[h1:2 * h1]
+    W2 = p[2 * h1:2 * h1 + h1 * h2].reshape(h2, h1)
+    b2 = p[2 * h1 + h1 * h2:2 * h1 + h1 * h2 + h2]
+    W3 = p[2 * h1 + h1 * h2 + h2:2 * h1 + h1 * h2 + 2 * h2]
+    b3 = p[-1]
+    w = keys_sample.astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = np.where(w & 0x80000000, ~w & 0xFFFFFFFF, w | 0x80000000)  # order image
+    lo = int(desc["lo_bits"])
+    d = np.where(u >= lo, (u - lo).astype(np.float64), -((lo - u).astype(np.float64)))
+    x = (d.astype(np.float32) * np.float32(desc["scale"])).astype(np.float64)
+    h = np.maximum(np.outer(x, W1) + b1, 0.0)
+    exact = np.maximum(h @ W2.T + b2, 0.0) @ W3 + b3
+    h32 = h.astype(np.float32)
+    hi = (h32.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32).astype(np.float64)
+    rest = np.float16(h32.astype(np.float64) - hi).astype(np.float64)
+    W2b = _bf16_rn(W2.astype(np.float32)).astype(np.float64)
+    W2h = np.float16(W2.astype(np.float32)).astype(np.float64)
+    W2r = _bf16_rn((W2.astype(np.float32) - W2b.astype(np.float32))).astype(np.float64)
+    out = {"sample_keys": int(keys_sample.size)}
+    for name, A, B in (("as the kernel (W2 in BF16 for the BF16 part, FP16 for the rest)", W2b, W2h),
+                       ("W2 carried as BF16 part + BF16 rest", W2b + W2r, W2h),
+                       ("exact W2 (activations split only)", W2, W2)):
+        y = np.maximum(hi @ A.T + rest @ B.T + b2, 0.0) @ W3 + b3
+        dd = np.abs(np.clip(y, 0.0, 1.0) - np.clip(exact, 0.0, 1.0)) * nm
+        out[name] = {"mean_abs": float(dd.mean()), "max_abs": float(dd.max())}
+    return out
+
+
 def run_job(nns, keys, precision, sopts, stats=True, timing=False):
     model, hist = nns.train(keys, **ARCH, **TRAIN)
     st = nns.sort(keys, None, model, precision=precision, stats=stats, timing=timing, **sopts)
@@ -1047,6 +1091,10 @@ def main():
             del sp, d
         slot_error["pwl"] = {"conflict_rate": w1["pwl"][1] / n if len(w1["pwl"]) > 1 else None}
         del ref
+        desc, params = model.describe()
+        if desc["layers"] == 2 and pristine.dtype == torch.float32:
+            slot_error["split_bf16_w2_rounding"] = w2_split_displacement(
+                pristine[::max(1, n >> 18)].cpu().numpy(), desc, params, n * SORT["m"])
 
     # roofline of the dominant kernel stage: its mean duration over the timed steps (events the
     # library records on the call's stream)
