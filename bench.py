@@ -47,8 +47,8 @@ WORKLOAD = ("268,435,456 float32 keys lognormal(0,2) with 5% exact duplicates, k
 TRAFFIC_PER_KEY = {
     ("predict", "bf16x2"): 7.363,   # k_predict_bf16_mg<64, split>
     ("partition", None): 19.78,     # per pass: k_tile_hist 4.22 + k_scatter 15.56
-    ("rounds", None): 6.80,         # k_rounds
-    ("polish", None): 12.66,        # k_polish
+    ("rounds", None): 6.79,         # k_rounds
+    ("polish", None): 12.58,        # k_polish
 }
 TRAFFIC_SOURCE = "ncu capture of the kernel at 2^26 keys, scaled to the launch's keys"
 # binary32 operations per key on the CUDA cores in the tensor-core predict (layer 1: H FMA; split
