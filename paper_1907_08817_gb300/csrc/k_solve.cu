@@ -1380,13 +1380,14 @@ __global__ void k_seam_cuts(SolveArgs a) {
 
 // 3) k_seam_emit (one block per array): the runs between consecutive sound cuts that hold two or
 //    more elements (backward: the next bucket's first sound cut).
-__global__ void __launch_bounds__(SOLVE_THREADS) k_seam_emit(SolveArgs a) {
-    __shared__ KMax ks[33];
-    __shared__ KMax tot;
-    const int s = blockIdx.x, tid = threadIdx.x;
+__global__ void __launch_bounds__(SCAN_THREADS) k_seam_emit(SolveArgs a) {
+    constexpr int NW = SCAN_THREADS / 32;
+    __shared__ unsigned long long wmin[NW];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (*a.err) return;
     const Seg &sg = a.segs[s];
     const uint32_t nb = sg.nb, bb = sg.bbase;
+    // a sound cut is a position below n, so NONE (all ones) is the identity of the minimum
     const unsigned long long n = sg.n, NONE = ~0ull;
     auto emit = [&](unsigned long long lo, unsigned long long hi) {
         if (hi - lo < 2) return;
@@ -1400,14 +1401,15 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_emit(SolveArgs a) {
             a.ranges[atomicAdd(&a.seam_cnt[0], 1u)] = r;
         }
     };
-    // tiles of PSI * SOLVE_THREADS buckets, PSI consecutive ones per thread (later ones first)
+    auto umin = [](unsigned long long x, unsigned long long y) { return y < x ? y : x; };
+    // tiles of PSI * SCAN_THREADS buckets, PSI consecutive ones per thread (later ones first)
     constexpr int PSI = 8;
-    constexpr uint32_t PST = SOLVE_THREADS * PSI;
-    KMax carry = kmax_none();  // smallest first sound cut after the current tile (inverted)
+    constexpr uint32_t PST = SCAN_THREADS * PSI;
+    unsigned long long carry = NONE;  // smallest first sound cut after the current tile
     for (uint32_t t1 = nb; t1 > 0;) {
         const uint32_t t0 = t1 > PST ? t1 - PST : 0;
         unsigned long long fg[PSI], lg[PSI];
-        KMax loc = kmax_none();
+        unsigned long long loc = NONE;
 #pragma unroll
         for (int k = 0; k < PSI; ++k) {
             const uint32_t r = (uint32_t)tid * PSI + k;
@@ -1415,24 +1417,37 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_seam_emit(SolveArgs a) {
             const uint32_t bi = bb + (t1 - 1 - r);
             fg[k] = own ? a.seam_cut[2 * (size_t)bi] : NONE;
             lg[k] = own ? a.seam_cut[2 * (size_t)bi + 1] : NONE;
-            if (fg[k] != NONE) {
-                KMax v; v.k = ~fg[k]; v.tb = 0; v.valid = 1;
-                loc = kmax(loc, v);
-            }
+            loc = umin(loc, fg[k]);
         }
-        KMax run = kmax(carry, block_excl_max(loc, ks, &tot));
+        // exclusive minimum over the threads before this one (they hold later buckets)
+        unsigned long long x = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x = umin(x, y);
+        }
+        unsigned long long ex = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+        if (lane == 0) ex = NONE;
+        if (lane == 31) wmin[wid] = x;
+        __syncthreads();
+        unsigned long long before = lane < wid ? wmin[lane] : NONE;
+        unsigned long long all = lane < NW ? wmin[lane] : NONE;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            before = umin(before, __shfl_xor_sync(0xFFFFFFFFu, before, o));
+            all = umin(all, __shfl_xor_sync(0xFFFFFFFFu, all, o));
+        }
+        __syncthreads();  // wmin is written again by the next tile
+        unsigned long long run = umin(carry, umin(before, ex));
 #pragma unroll
         for (int k = 0; k < PSI; ++k) {
-            if (lg[k] != NONE) emit(lg[k], run.valid ? ~run.k : n);
-            if (fg[k] != NONE) {
-                KMax v; v.k = ~fg[k]; v.tb = 0; v.valid = 1;
-                run = kmax(run, v);
-            }
+            if (lg[k] != NONE) emit(lg[k], run != NONE ? run : n);
+            run = umin(run, fg[k]);
         }
-        carry = kmax(carry, tot);
+        carry = umin(carry, all);
         t1 = t0;
     }
-    if (tid == 0) emit(0, carry.valid ? ~carry.k : n);  // before the first sound cut
+    if (tid == 0) emit(0, carry != NONE ? carry : n);  // before the first sound cut
 }
 
 // re-sort out[lo, lo + len) of one array by (key, row): the range is a union of sorted runs. The
@@ -1673,7 +1688,7 @@ template <typename W> static cudaError_t seam_go(const SolveArgs &a, int sms, cu
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
     k_seam_cuts<W><<<(a.NB + 255) / 256, 256, 0, s>>>(a);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
-    k_seam_emit<<<a.nseg, SOLVE_THREADS, 0, s>>>(a);
+    k_seam_emit<<<a.nseg, SCAN_THREADS, 0, s>>>(a);
     if ((e = nns_launched(cudaGetLastError())) != cudaSuccess) return e;
     const size_t fix_smem = ((sizeof(PolishSmem) + 15) & ~(size_t)15) + 2 * sizeof(uint32_t) * SEAM_SMEM_IDX;
     if ((e = cudaFuncSetAttribute(k_seam_fix<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fix_smem)) !=
